@@ -1,0 +1,198 @@
+/*
+ * hisq.h -- C ABI of the GB300 library for deflated HISQ propagator solves.
+ *
+ * Method: "Improving HISQ propagator solves using deflation" (Hostetler, Clark,
+ * DeTar, Gottlieb, Weinberg; LATTICE2024).
+ *   Section 2      M = D + 2m, D the anti-Hermitian HISQ Dirac matrix (one-hop fat
+ *                  links, three-hop Naik "long" links); CG on the normal equation
+ *                  M^dag M psi = M^dag eta (Eq. 1), even-odd preconditioned:
+ *                  y_e = (M^dag eta)_e, solve (M^dag M)_ee psi_e = y_e, then
+ *                  reconstruct the odd sites.
+ *   Section 2      Low eigenvectors of the squared massless operator by
+ *                  thick-restart Lanczos; deflated initial guess
+ *                  x = sum_i v_i lambda_i^-1 v_i^dag b (Eq. 4), with
+ *                  lambda_i = eps_i + (2m)^2 (Eq. 3).
+ *   Section 3      Mixed precision with reliable updates (delta_rd = 0.1) and
+ *                  re-deflation whenever the residual drops by 1/delta_tr since the
+ *                  last deflation (delta_tr = 1e-3), with single-precision
+ *                  eigenvectors.
+ *
+ * Operator convention (the paper fixes neither the factor 1/2 nor the hop signs):
+ *   (D psi)(x) = sum_mu eta_mu(x) [ F_mu(x) psi(x+mu) - F_mu(x-mu)^dag psi(x-mu)
+ *                                 + L_mu(x) psi(x+3mu) - L_mu(x-3mu)^dag psi(x-3mu) ]
+ *   eta_x = 1, eta_y = (-1)^x, eta_z = (-1)^(x+y), eta_t = (-1)^(x+y+z);
+ *   periodic in space; in time periodic or antiperiodic (a hop that wraps from
+ *   t = T-1 to t = 0 carries a factor -1).  The HISQ coefficients are folded into
+ *   the links the caller passes (fat = c1 * ..., long = c3 * ...).
+ *   Odd reconstruction: psi_o = (eta_o - D_oe psi_e) / (2m).
+ *
+ * Host layouts (FP64, caller-owned, copied during the call):
+ *   site index s = x + X*(y + Y*(z + Z*t)); parity (x+y+z+t) mod 2, even = 0;
+ *   links  [s][mu][row][col][re,im]  (mu = x, y, z, t), V*4*18 doubles;
+ *   fields [s][colour][re,im] over the full lattice, V*6 doubles.
+ * Device-pointer variants (*_device) take the same layouts in device memory,
+ * owned by the caller; the library never frees caller memory.
+ *
+ * Errors: every call returns a hisq_status; the context keeps a message for the
+ * last error (hisq_last_error).  A call that fails with HISQ_ERR_CUDA leaves the
+ * context in an undefined state: destroy it.  Contexts are not thread-safe; all
+ * work of one context runs in order on its stream.
+ */
+#ifndef HISQ_H
+#define HISQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hisq_ctx hisq_ctx;
+
+typedef enum {
+    HISQ_OK = 0,
+    HISQ_ERR_INVALID_ARG = 1,   /* bad size, pointer, precision or parameter       */
+    HISQ_ERR_CUDA = 2,          /* a CUDA runtime call failed                      */
+    HISQ_ERR_OOM = 3,           /* device or pinned host allocation failed         */
+    HISQ_ERR_NOT_CONVERGED = 4, /* max_iter reached; psi holds the best iterate    */
+    HISQ_ERR_NUMERICAL = 5,     /* NaN/Inf in a reduction or an input              */
+    HISQ_ERR_TIMEOUT = 6,       /* a bounded device wait ran out                    */
+    HISQ_ERR_STATE = 7          /* call order violated (e.g. solve before links)   */
+} hisq_status;
+
+/* Storage precisions.  Arithmetic is FP64 for HISQ_PREC_DOUBLE and FP32 otherwise. */
+typedef enum {
+    HISQ_PREC_DOUBLE = 64,
+    HISQ_PREC_SINGLE = 32,
+    HISQ_PREC_HALF = 16 /* FP16 values with one FP32 scale per site (colour vectors) */
+} hisq_precision;
+
+/* Parameters of a propagator solve (Sections 2 and 3). */
+typedef struct {
+    double tol;              /* stop when |y_e - A psi_e| <= tol * min(|y_e|, 2m|eta|)
+                                (FP64 true residual); 1e-10 in the benchmarks      */
+    int max_iter;            /* sloppy CG iterations per right-hand side            */
+    int precision_sloppy;    /* colour-vector storage of the sloppy CG: 64, 32, 16 */
+    int link_precision_sloppy; /* link storage of the sloppy operator: 64 or 32     */
+    double delta_rd;         /* reliable update when |r| < delta_rd * |r_last|; 0.1 */
+    int deflate;             /* 1: deflated initial guess from the stored eigenpairs */
+    int n_defl;              /* eigenpairs used (<= stored); 0 = all stored         */
+    double delta_tr;         /* re-deflate when |r| < delta_tr * |r_defl|; 0 = off  */
+    int compute_full_residual; /* 1: also return |eta - M psi| / |eta| in FP64     */
+} hisq_solve_params;
+
+/* Per right-hand-side results of a solve. */
+typedef struct {
+    int iterations;          /* sloppy CG iterations                               */
+    int reliable_updates;    /* FP64 true-residual recomputations                  */
+    int redeflations;        /* deflations after the initial guess                 */
+    int converged;           /* 1 if the tolerance was met                         */
+    double even_residual;    /* |y_e - A psi_e| / |y_e|, FP64                      */
+    double full_residual;    /* |eta - M psi| / |eta|, FP64 (if requested, else -1) */
+    double seconds_total;    /* prep + deflation + CG + reconstruction             */
+    double seconds_deflate;  /* initial deflation and re-deflations                */
+} hisq_solve_stats;
+
+/* Parameters of the thick-restart Lanczos eigensolve (Section 2). */
+typedef struct {
+    int n_ev;                /* wanted eigenpairs (lowest of the squared operator)  */
+    int n_kr;                /* Krylov basis size, > n_ev + 8                       */
+    int n_keep;              /* vectors kept at a restart (0 = (n_ev + n_kr) / 2)    */
+    double tol;              /* Ritz residual |A v - theta v| <= tol * a_max        */
+    int max_restarts;
+    int cheby_degree;        /* Chebyshev filter degree (0 = Lanczos on A itself)   */
+    double a_min;            /* filter window [a_min, a_max] of the massless        */
+    double a_max;            /*   operator; <= 0: estimated                         */
+    int storage_precision;   /* eigenvector storage: 32 or 16                        */
+    uint64_t seed;           /* start vector                                        */
+} hisq_eig_params;
+
+/* Fill the structs with the paper's defaults (Section 3: delta_rd = 0.1,
+ * delta_tr = 1e-3; tolerance 1e-10). */
+void hisq_default_solve_params(hisq_solve_params *p);
+void hisq_default_eig_params(hisq_eig_params *p);
+
+/* Create a context on CUDA device `device` for an X*Y*Z*T lattice (each extent
+ * even and >= 4).  `cuda_stream` is a cudaStream_t or NULL (the context creates
+ * its own).  On success *out owns all device memory of the context. */
+hisq_status hisq_create(const int dims[4], int t_antiperiodic, int device, void *cuda_stream,
+                        hisq_ctx **out);
+void hisq_destroy(hisq_ctx *ctx);
+const char *hisq_last_error(const hisq_ctx *ctx);
+const char *hisq_status_string(hisq_status s);
+
+/* Load the fat (one-hop) and long (three-hop) links, FP64 host layout above,
+ * coefficients folded in.  long_recon = 18 stores all 18 reals of the long links;
+ * 12 stores two rows of long/long_scale (which must then be SU(3) to 1e-6;
+ * otherwise HISQ_ERR_INVALID_ARG) and rebuilds the third row on the fly.  The
+ * library folds staggered phases, boundary signs and the backward adjoints into
+ * its own device copies (FP64 and FP32).  Non-finite input: HISQ_ERR_NUMERICAL. */
+hisq_status hisq_load_links(hisq_ctx *ctx, const double *fat, const double *lng, int long_recon,
+                            double long_scale);
+
+/* Set the bare mass m > 0 (M = D + 2m).  Stored eigenvalues follow Eq. 3. */
+hisq_status hisq_set_mass(hisq_ctx *ctx, double m);
+
+/* out_parity sites of `out` = D applied to the opposite-parity sites of `in`
+ * (host full-lattice fields); the other parity of `out` is set to zero.
+ * precision 64: FP64 links and vectors; 32: FP32; 16: FP16 vectors, FP32 links.
+ * Test and diagnostic entry point. */
+hisq_status hisq_apply_dslash(hisq_ctx *ctx, int out_parity, int precision, const double *in,
+                              double *out);
+
+/* Even sites of `out` = (M^dag M)_ee applied to the even sites of `in`
+ * (= 4m^2 in_e - D_eo D_oe in_e); odd sites of `out` are zero. */
+hisq_status hisq_apply_normal_op(hisq_ctx *ctx, int precision, const double *in, double *out);
+
+/* Solve M psi_k = eta_k for nrhs right-hand sides (host full-lattice fields,
+ * right-hand side k at offset k*V*6 doubles).  stats: nrhs entries (nullable).
+ * Returns HISQ_ERR_NOT_CONVERGED if any right-hand side missed the tolerance. */
+hisq_status hisq_solve(hisq_ctx *ctx, const double *eta, double *psi, int nrhs,
+                       const hisq_solve_params *params, hisq_solve_stats *stats);
+
+/* As hisq_solve, with eta and psi in caller-owned device memory, ordered on the
+ * context's stream. */
+hisq_status hisq_solve_device(hisq_ctx *ctx, const double *eta_dev, double *psi_dev, int nrhs,
+                              const hisq_solve_params *params, hisq_solve_stats *stats);
+
+/* Thick-restart Lanczos for the lowest n_ev eigenpairs of the massless even-site
+ * operator -D_eo D_oe (Section 2), with FP32 operator and basis, FP64
+ * Rayleigh-Ritz on the host, and final FP64 Rayleigh quotients with the FP64
+ * operator (Section 3, eigenvalues recomputed from the eigenvectors).  eps_out
+ * (nullable, n_ev doubles) receives the massless eigenvalues eps_i in ascending
+ * order; *n_conv the number that met the tolerance.  The eigenvectors stay on
+ * the device for deflation. */
+hisq_status hisq_eigensolve(hisq_ctx *ctx, const hisq_eig_params *params, int *n_conv,
+                            double *eps_out);
+
+/* Number of stored eigenpairs and their massless eigenvalues (ascending). */
+hisq_status hisq_get_eigvals(hisq_ctx *ctx, int *n_ev, double *eps_out);
+
+/* Copy stored eigenvector i to a host full-lattice field (odd sites zero). */
+hisq_status hisq_get_eigvec(hisq_ctx *ctx, int i, double *out);
+
+/* Replace the stored eigenpairs by n host fields (even sites used; orthonormal)
+ * with massless eigenvalues eps (nullable: recomputed as FP64 Rayleigh
+ * quotients), stored at storage_precision 32 or 16. */
+hisq_status hisq_set_eigvecs(hisq_ctx *ctx, int n, const double *vecs, const double *eps,
+                             int storage_precision);
+
+/* x_e = sum_i v_i lambda_i^-1 v_i^dag b_e (Eq. 4) over the first n stored pairs
+ * (0 = all), lambda_i = eps_i + 4m^2; host full-lattice fields, even sites. */
+hisq_status hisq_deflate(hisq_ctx *ctx, int n, const double *b, double *x);
+
+/* Write / read the stored eigenpairs to / from a binary file (header with
+ * lattice, count, precision and checksum).  Loading recomputes the eigenvalues
+ * as FP64 Rayleigh quotients (Section 3). */
+hisq_status hisq_save_eigvecs(hisq_ctx *ctx, const char *path);
+hisq_status hisq_load_eigvecs(hisq_ctx *ctx, const char *path);
+
+/* Device bytes held by the context. */
+size_t hisq_device_bytes(const hisq_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HISQ_H */

@@ -1,0 +1,292 @@
+// dslash.cu -- the HISQ Dirac operator on one parity (Section 2 of the paper:
+// M = D + 2m, D with one-hop fat links and three-hop Naik long links) and the
+// fused kernels of one CG iteration on (M^dag M)_ee = 4m^2 - D_eo D_oe (Eq. 1).
+//
+// One thread computes one output site: 16 link matrices are streamed from the
+// gathered per-parity link arrays (read once per half-apply, evict-first), the
+// 16 neighbour colour vectors are gathered from the opposite parity (they stay
+// in L2: a parity field is at most a few hundred MB and the sweep order keeps
+// the +-3 time-slice window resident).
+#include "internal.cuh"
+
+namespace hisq {
+
+// ------------------------------------------------------------- epilogues
+// out = a*x + b*y + c*acc; optional |out|^2
+template <class S>
+struct EpiXpay {
+    S out, x, y;
+    typename S::real a, b, c;
+    int has_x, has_y, want_norm;
+    template <typename R>
+    __device__ __forceinline__ void operator()(int cb, const CVec<R> &acc, double &red) const
+    {
+        CVec<R> o;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            o.re[i] = c * acc.re[i];
+            o.im[i] = c * acc.im[i];
+        }
+        if (has_x) {
+            CVec<R> v = x.load(cb);
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                o.re[i] = fma(a, v.re[i], o.re[i]);
+                o.im[i] = fma(a, v.im[i], o.im[i]);
+            }
+        }
+        if (has_y) {
+            CVec<R> v = y.load(cb);
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                o.re[i] = fma(b, v.re[i], o.re[i]);
+                o.im[i] = fma(b, v.im[i], o.im[i]);
+            }
+        }
+        out.store(cb, o);
+        if (want_norm) red += double(o.norm2());
+    }
+};
+
+// second half of a CG iteration: Ap = 4m^2 p - D_eo tmp; x += alpha p;
+// r -= alpha Ap; |r|^2.  Ap is never stored.
+template <class S, class SX>
+struct EpiCG {
+    S p, r;
+    SX x;
+    const DevScalars *scal;
+    template <typename R>
+    __device__ __forceinline__ void operator()(int cb, const CVec<R> &acc, double &red) const
+    {
+        const R alpha = R(scal->alpha);
+        const R m4 = R(scal->m4);
+        CVec<R> pv = p.load(cb);
+        CVec<R> rv = r.load(cb);
+        auto xv = x.load(cb);
+        typedef typename SX::real XR;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            R apr = fma(m4, pv.re[i], -acc.re[i]);
+            R api = fma(m4, pv.im[i], -acc.im[i]);
+            rv.re[i] = fma(-alpha, apr, rv.re[i]);
+            rv.im[i] = fma(-alpha, api, rv.im[i]);
+            xv.re[i] = fma(XR(alpha), XR(pv.re[i]), xv.re[i]);
+            xv.im[i] = fma(XR(alpha), XR(pv.im[i]), xv.im[i]);
+        }
+        x.store(cb, xv);
+        r.store(cb, rv);
+        red += double(rv.norm2());
+    }
+};
+
+// ------------------------------------------------------------- the kernel
+template <class SIn, class Lk, bool R12, class Epi>
+__global__ void __launch_bounds__(256)
+    k_dslash(Geom g, int par, Lk L, LinksF12 L12, float c3, SIn in, Epi epi, RedArgs ra, int do_red)
+{
+    typedef typename Lk::real R;
+    double red = 0;
+    for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < g.Vh; cb += gridDim.x * blockDim.x) {
+        int c[4];
+        cb_coords(g, par, cb, c);
+        const int s = full_site(g, c);
+        CVec<R> acc;
+        acc.zero();
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) {
+            CMat<R> f, b;
+            L.load(mu, 0, cb, f, b);
+            {
+                CVec<R> vf = cvt<R>(in.load(nb_cb(g, c, s, mu, +1)));
+                CVec<R> vb = cvt<R>(in.load(nb_cb(g, c, s, mu, -1)));
+                mv_acc(acc, f, vf);
+                mv_acc(acc, b, vb);
+            }
+            if constexpr (R12) {
+                CMat<float> f3, b3;
+                L12.load(mu, cb, f3, b3);
+                const float eta = stag_phase(mu, c);
+                float sf = eta * c3, sb = -eta * c3;
+                if (mu == 3 && g.t_antiperiodic) {
+                    if (c[3] + 3 >= g.T) sf = -sf;
+                    if (c[3] < 3) sb = -sb;
+                }
+                CVec<float> vf = cvt<float>(in.load(nb_cb(g, c, s, mu, +3)));
+                CVec<float> vb = cvt<float>(in.load(nb_cb(g, c, s, mu, -3)));
+                mv_acc_scaled(acc, sf, f3, vf);
+                mv_acc_scaled(acc, sb, b3, vb);
+            } else {
+                L.load(mu, 1, cb, f, b);
+                CVec<R> vf = cvt<R>(in.load(nb_cb(g, c, s, mu, +3)));
+                CVec<R> vb = cvt<R>(in.load(nb_cb(g, c, s, mu, -3)));
+                mv_acc(acc, f, vf);
+                mv_acc(acc, b, vb);
+            }
+        }
+        epi(cb, acc, red);
+    }
+    if (do_red) {
+        double v[1] = {red};
+        grid_reduce<1>(v, ra);
+    }
+}
+
+// ------------------------------------------------------------- launch glue
+template <typename K>
+static int blocks_per_sm(K kernel)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, 256, 0) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
+template <class SIn, class Lk, bool R12, class Epi>
+static hisq_status run_dslash(hisq_ctx *ctx, int par, const Lk &L, const SIn &in, const Epi &epi,
+                              RedArgs ra, int do_red)
+{
+    auto kern = k_dslash<SIn, Lk, R12, Epi>;
+    static int bps = -1;
+    if (bps < 0) bps = blocks_per_sm(kern);
+    const int grid = grid_for(ctx, ctx->g.Vh, 256, bps);
+    LinksF12 l12{nullptr, ctx->g.Vh};
+    if (R12) l12.base = ctx->links_f12[par];
+    kern<<<grid, 256, 0, ctx->stream>>>(ctx->g, par, L, l12, float(ctx->long_scale), in, epi, ra, do_red);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(ctx, e, "dslash launch");
+    return HISQ_OK;
+}
+
+static LinksD links_d(hisq_ctx *ctx, int par) { return LinksD{ctx->links_d[par], ctx->g.Vh}; }
+
+struct LinksFv { // FP32 links, kinds per mu = 2 (recon 18) or 1 (fat only, recon 12)
+    const float4 *base;
+    int Vh;
+    int nk;
+    typedef float real;
+    __device__ __forceinline__ void load(int mu, int kind, int i, CMat<float> &f, CMat<float> &b) const
+    {
+        const float4 *q = base + size_t((mu * nk + kind) * 9) * Vh + i;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            float4 a = __ldcs(q + size_t(k) * Vh);
+            f.re[k] = a.x;
+            f.im[k] = a.y;
+            b.re[k] = a.z;
+            b.im[k] = a.w;
+        }
+    }
+};
+
+static LinksFv links_f(hisq_ctx *ctx, int par)
+{
+    return LinksFv{ctx->links_f[par], ctx->g.Vh, ctx->long_recon == 12 ? 1 : 2};
+}
+
+template <class S>
+static hisq_status dslash_prec(hisq_ctx *ctx, int par, int link_prec, S in, S out, double a, const void *x,
+                               double b, const void *y, double c, int norm_slot, S sx, S sy)
+{
+    typedef typename S::real R;
+    EpiXpay<S> epi{out, sx, sy, R(a), R(b), R(c), x != nullptr, y != nullptr, norm_slot >= 0};
+    RedArgs ra = red_args(ctx, FIN_STORE, norm_slot < 0 ? 0 : norm_slot);
+    const int dored = norm_slot >= 0;
+    const int inpar = par; // output parity; links indexed by output parity
+    if (link_prec == 64) {
+        if constexpr (sizeof(R) == 8) return run_dslash<S, LinksD, false>(ctx, inpar, links_d(ctx, par), in, epi, ra, dored);
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "FP64 links need FP64 vectors");
+    }
+    if constexpr (sizeof(R) == 4) {
+        if (ctx->long_recon == 12)
+            return run_dslash<S, LinksFv, true>(ctx, inpar, links_f(ctx, par), in, epi, ra, dored);
+        return run_dslash<S, LinksFv, false>(ctx, inpar, links_f(ctx, par), in, epi, ra, dored);
+    }
+    return set_err(ctx, HISQ_ERR_INVALID_ARG, "FP32 links need FP32 or FP16 vectors");
+}
+
+hisq_status launch_dslash(hisq_ctx *ctx, int out_parity, int prec, int link_prec, const void *in, void *out,
+                          double a, const void *x, double b, const void *y, double c, int norm_slot)
+{
+    const int Vh = ctx->g.Vh;
+    if (!ctx->links_loaded) return set_err(ctx, HISQ_ERR_STATE, "links not loaded");
+    void *xx = const_cast<void *>(x ? x : out), *yy = const_cast<void *>(y ? y : out);
+    switch (prec) {
+    case 64:
+        if (link_prec != 64) return set_err(ctx, HISQ_ERR_INVALID_ARG, "FP64 vectors need FP64 links");
+        return dslash_prec<SpinorD>(ctx, out_parity, 64, make_spinorD(const_cast<void *>(in), Vh),
+                                    make_spinorD(out, Vh), a, x, b, y, c, norm_slot, make_spinorD(xx, Vh),
+                                    make_spinorD(yy, Vh));
+    case 32:
+        return dslash_prec<SpinorF>(ctx, out_parity, 32, make_spinorF(const_cast<void *>(in), Vh),
+                                    make_spinorF(out, Vh), a, x, b, y, c, norm_slot, make_spinorF(xx, Vh),
+                                    make_spinorF(yy, Vh));
+    case 16:
+        return dslash_prec<SpinorH>(ctx, out_parity, 32, make_spinorH(const_cast<void *>(in), Vh),
+                                    make_spinorH(out, Vh), a, x, b, y, c, norm_slot, make_spinorH(xx, Vh),
+                                    make_spinorH(yy, Vh));
+    }
+    return set_err(ctx, HISQ_ERR_INVALID_ARG, "precision must be 64, 32 or 16");
+}
+
+// ---------------------------------------------------------- CG iteration
+// (1) tmp = D_oe p (odd output) with tt = |tmp|^2 -> alpha = rr / (4m^2 pp + tt)
+//     using <p, A p> = 4m^2 |p|^2 + |D_oe p|^2 (D_eo = -D_oe^dag).
+hisq_status launch_cg_dslash_tt(hisq_ctx *ctx, int prec, int link_prec, const void *p, void *tmp)
+{
+    const int Vh = ctx->g.Vh;
+    RedArgs ra = red_args(ctx, FIN_CG_ALPHA);
+    switch (prec) {
+    case 64: {
+        SpinorD in = make_spinorD(const_cast<void *>(p), Vh), out = make_spinorD(tmp, Vh);
+        EpiXpay<SpinorD> epi{out, out, out, 0.0, 0.0, 1.0, 0, 0, 1};
+        return run_dslash<SpinorD, LinksD, false>(ctx, 1, links_d(ctx, 1), in, epi, ra, 1);
+    }
+    case 32: {
+        SpinorF in = make_spinorF(const_cast<void *>(p), Vh), out = make_spinorF(tmp, Vh);
+        EpiXpay<SpinorF> epi{out, out, out, 0.f, 0.f, 1.f, 0, 0, 1};
+        if (ctx->long_recon == 12) return run_dslash<SpinorF, LinksFv, true>(ctx, 1, links_f(ctx, 1), in, epi, ra, 1);
+        return run_dslash<SpinorF, LinksFv, false>(ctx, 1, links_f(ctx, 1), in, epi, ra, 1);
+    }
+    case 16: {
+        SpinorH in = make_spinorH(const_cast<void *>(p), Vh), out = make_spinorH(tmp, Vh);
+        EpiXpay<SpinorH> epi{out, out, out, 0.f, 0.f, 1.f, 0, 0, 1};
+        if (ctx->long_recon == 12) return run_dslash<SpinorH, LinksFv, true>(ctx, 1, links_f(ctx, 1), in, epi, ra, 1);
+        return run_dslash<SpinorH, LinksFv, false>(ctx, 1, links_f(ctx, 1), in, epi, ra, 1);
+    }
+    }
+    (void)link_prec;
+    return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad sloppy precision");
+}
+
+// (2) even output: Ap = 4m^2 p - D_eo tmp; x += alpha p; r -= alpha Ap; rr_new = |r|^2,
+//     beta = rr_new / rr.
+hisq_status launch_cg_dslash_update(hisq_ctx *ctx, int prec, int link_prec, int xprec, const void *tmp,
+                                    const void *p, void *x, void *r)
+{
+    const int Vh = ctx->g.Vh;
+    RedArgs ra = red_args(ctx, FIN_CG_BETA);
+    (void)link_prec;
+    switch (prec) {
+    case 64: {
+        SpinorD in = make_spinorD(const_cast<void *>(tmp), Vh);
+        EpiCG<SpinorD, SpinorD> epi{make_spinorD(const_cast<void *>(p), Vh), make_spinorD(r, Vh), make_spinorD(x, Vh), ctx->scal};
+        return run_dslash<SpinorD, LinksD, false>(ctx, 0, links_d(ctx, 0), in, epi, ra, 1);
+    }
+    case 32: {
+        SpinorF in = make_spinorF(const_cast<void *>(tmp), Vh);
+        if (xprec != 32) return set_err(ctx, HISQ_ERR_INVALID_ARG, "x precision");
+        EpiCG<SpinorF, SpinorF> epi{make_spinorF(const_cast<void *>(p), Vh), make_spinorF(r, Vh), make_spinorF(x, Vh), ctx->scal};
+        if (ctx->long_recon == 12) return run_dslash<SpinorF, LinksFv, true>(ctx, 0, links_f(ctx, 0), in, epi, ra, 1);
+        return run_dslash<SpinorF, LinksFv, false>(ctx, 0, links_f(ctx, 0), in, epi, ra, 1);
+    }
+    case 16: {
+        SpinorH in = make_spinorH(const_cast<void *>(tmp), Vh);
+        if (xprec != 32) return set_err(ctx, HISQ_ERR_INVALID_ARG, "x precision");
+        EpiCG<SpinorH, SpinorF> epi{make_spinorH(const_cast<void *>(p), Vh), make_spinorH(r, Vh), make_spinorF(x, Vh), ctx->scal};
+        if (ctx->long_recon == 12) return run_dslash<SpinorH, LinksFv, true>(ctx, 0, links_f(ctx, 0), in, epi, ra, 1);
+        return run_dslash<SpinorH, LinksFv, false>(ctx, 0, links_f(ctx, 0), in, epi, ra, 1);
+    }
+    }
+    return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad sloppy precision");
+}
+
+} // namespace hisq

@@ -1,0 +1,603 @@
+// internal.cuh -- shared device types of the HISQ library: complex colour
+// vectors and matrices, lattice geometry on one parity, storage formats of
+// colour vectors and of the gathered link fields, and the deterministic
+// grid-wide reduction used by every norm and inner product.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/hisq.h"
+
+namespace hisq {
+
+// ------------------------------------------------------------------ complex
+template <typename T>
+struct Cplx {
+    T re, im;
+};
+
+template <typename T>
+__host__ __device__ __forceinline__ Cplx<T> cmul(Cplx<T> a, Cplx<T> b)
+{
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+
+// colour vector: 3 complex numbers
+template <typename T>
+struct CVec {
+    T re[3], im[3];
+    __host__ __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int i = 0; i < 3; i++) re[i] = im[i] = T(0);
+    }
+    __host__ __device__ __forceinline__ T norm2() const
+    {
+        T s = 0;
+#pragma unroll
+        for (int i = 0; i < 3; i++) s += re[i] * re[i] + im[i] * im[i];
+        return s;
+    }
+};
+
+// colour matrix, row major
+template <typename T>
+struct CMat {
+    T re[9], im[9];
+};
+
+// acc += W v
+template <typename T>
+__device__ __forceinline__ void mv_acc(CVec<T> &acc, const CMat<T> &W, const CVec<T> &v)
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            acc.re[i] = fma(W.re[3 * i + j], v.re[j], acc.re[i]);
+            acc.re[i] = fma(-W.im[3 * i + j], v.im[j], acc.re[i]);
+            acc.im[i] = fma(W.re[3 * i + j], v.im[j], acc.im[i]);
+            acc.im[i] = fma(W.im[3 * i + j], v.re[j], acc.im[i]);
+        }
+    }
+}
+
+// acc += s * (W v), s real
+template <typename T>
+__device__ __forceinline__ void mv_acc_scaled(CVec<T> &acc, T s, const CMat<T> &W, const CVec<T> &v)
+{
+    CVec<T> t;
+    t.zero();
+    mv_acc(t, W, v);
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        acc.re[i] = fma(s, t.re[i], acc.re[i]);
+        acc.im[i] = fma(s, t.im[i], acc.im[i]);
+    }
+}
+
+// third row of an SU(3) matrix from the first two: row2 = conj(row0 x row1)
+template <typename T>
+__device__ __forceinline__ void su3_third_row(CMat<T> &W)
+{
+    // (a x b)_k = a_{k+1} b_{k+2} - a_{k+2} b_{k+1}
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+        T are1 = W.re[k1], aim1 = W.im[k1], are2 = W.re[k2], aim2 = W.im[k2];
+        T bre1 = W.re[3 + k1], bim1 = W.im[3 + k1], bre2 = W.re[3 + k2], bim2 = W.im[3 + k2];
+        T cre = (are1 * bre2 - aim1 * bim2) - (are2 * bre1 - aim2 * bim1);
+        T cim = (are1 * bim2 + aim1 * bre2) - (are2 * bim1 + aim2 * bre1);
+        W.re[6 + k] = cre;
+        W.im[6 + k] = -cim;
+    }
+}
+
+// ---------------------------------------------------------------- geometry
+struct Geom {
+    int X, Y, Z, T;
+    int X2;          // X / 2
+    int Vh;          // sites of one parity
+    int V;
+    int t_antiperiodic;
+    int stride[4];   // 1, X, XY, XYZ (full-lattice site index)
+};
+
+// coordinates of checkerboard site cb of parity `par` (cb = s >> 1)
+__device__ __forceinline__ void cb_coords(const Geom &g, int par, int cb, int c[4])
+{
+    int xh = cb % g.X2;
+    int r = cb / g.X2;
+    c[1] = r % g.Y;
+    r /= g.Y;
+    c[2] = r % g.Z;
+    c[3] = r / g.Z;
+    c[0] = 2 * xh + ((par + c[1] + c[2] + c[3]) & 1);
+}
+
+__device__ __forceinline__ int dim_of(const Geom &g, int mu)
+{
+    return mu == 0 ? g.X : (mu == 1 ? g.Y : (mu == 2 ? g.Z : g.T));
+}
+
+// checkerboard index of the site c + d * mu_hat (periodic wrap); |d| <= 3 < L
+__device__ __forceinline__ int nb_cb(const Geom &g, const int c[4], int s, int mu, int d)
+{
+    const int L = dim_of(g, mu);
+    int cn = c[mu] + d;
+    cn += (cn < 0) ? L : 0;
+    cn -= (cn >= L) ? L : 0;
+    return (s + (cn - c[mu]) * g.stride[mu]) >> 1;
+}
+
+__device__ __forceinline__ int full_site(const Geom &g, const int c[4])
+{
+    return c[0] + g.X * (c[1] + g.Y * (c[2] + g.Z * c[3]));
+}
+
+// staggered phase eta_mu(x) = (-1)^(x_0 + ... + x_{mu-1})
+__device__ __forceinline__ float stag_phase(int mu, const int c[4])
+{
+    int e = 0;
+    if (mu > 0) e += c[0];
+    if (mu > 1) e += c[1];
+    if (mu > 2) e += c[2];
+    return (e & 1) ? -1.f : 1.f;
+}
+
+// ----------------------------------------------------- colour-vector storage
+// One parity of a colour field, Vh sites.
+//  FP64: [3][Vh] double2                       48 B / site
+//  FP32: [Vh] float4 (colours 0,1) then [Vh] float2 (colour 2)   24 B / site
+//  FP16: [Vh] uint4 = 6 halves (re,im x 3) + FP32 scale          16 B / site
+inline size_t spinor_bytes(int prec, int Vh)
+{
+    return prec == 64 ? size_t(Vh) * 48 : (prec == 32 ? size_t(Vh) * 24 : size_t(Vh) * 16);
+}
+
+struct SpinorD {
+    double2 *p;
+    int Vh;
+    typedef double real;
+    __device__ __forceinline__ CVec<double> load(int i) const
+    {
+        CVec<double> v;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            double2 a = p[size_t(c) * Vh + i];
+            v.re[c] = a.x;
+            v.im[c] = a.y;
+        }
+        return v;
+    }
+    __device__ __forceinline__ void store(int i, const CVec<double> &v) const
+    {
+#pragma unroll
+        for (int c = 0; c < 3; c++) p[size_t(c) * Vh + i] = make_double2(v.re[c], v.im[c]);
+    }
+};
+
+struct SpinorF {
+    float4 *a;
+    float2 *b;
+    int Vh;
+    typedef float real;
+    __device__ __forceinline__ CVec<float> load(int i) const
+    {
+        float4 u = a[i];
+        float2 w = b[i];
+        CVec<float> v;
+        v.re[0] = u.x;
+        v.im[0] = u.y;
+        v.re[1] = u.z;
+        v.im[1] = u.w;
+        v.re[2] = w.x;
+        v.im[2] = w.y;
+        return v;
+    }
+    __device__ __forceinline__ void store(int i, const CVec<float> &v) const
+    {
+        a[i] = make_float4(v.re[0], v.im[0], v.re[1], v.im[1]);
+        b[i] = make_float2(v.re[2], v.im[2]);
+    }
+};
+
+struct SpinorH {
+    uint4 *p;
+    int Vh;
+    typedef float real;
+    __device__ __forceinline__ CVec<float> load(int i) const
+    {
+        uint4 u = p[i];
+        const float s = __uint_as_float(u.w);
+        __half2 h0 = *reinterpret_cast<__half2 *>(&u.x);
+        __half2 h1 = *reinterpret_cast<__half2 *>(&u.y);
+        __half2 h2 = *reinterpret_cast<__half2 *>(&u.z);
+        float2 f0 = __half22float2(h0), f1 = __half22float2(h1), f2 = __half22float2(h2);
+        CVec<float> v;
+        v.re[0] = f0.x * s;
+        v.im[0] = f0.y * s;
+        v.re[1] = f1.x * s;
+        v.im[1] = f1.y * s;
+        v.re[2] = f2.x * s;
+        v.im[2] = f2.y * s;
+        return v;
+    }
+    __device__ __forceinline__ void store(int i, const CVec<float> &v) const
+    {
+        float m = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; c++) m = fmaxf(m, fmaxf(fabsf(v.re[c]), fabsf(v.im[c])));
+        const float inv = m > 0.f ? 1.0f / m : 0.f;
+        __half2 h0 = __floats2half2_rn(v.re[0] * inv, v.im[0] * inv);
+        __half2 h1 = __floats2half2_rn(v.re[1] * inv, v.im[1] * inv);
+        __half2 h2 = __floats2half2_rn(v.re[2] * inv, v.im[2] * inv);
+        uint4 u;
+        u.x = *reinterpret_cast<unsigned *>(&h0);
+        u.y = *reinterpret_cast<unsigned *>(&h1);
+        u.z = *reinterpret_cast<unsigned *>(&h2);
+        u.w = __float_as_uint(m);
+        p[i] = u;
+    }
+};
+
+inline SpinorD make_spinorD(void *p, int Vh) { return SpinorD{(double2 *)p, Vh}; }
+inline SpinorF make_spinorF(void *p, int Vh) { return SpinorF{(float4 *)p, (float2 *)((char *)p + size_t(Vh) * 16), Vh}; }
+inline SpinorH make_spinorH(void *p, int Vh) { return SpinorH{(uint4 *)p, Vh}; }
+
+// convert between accumulation types
+template <typename To, typename From>
+__device__ __forceinline__ CVec<To> cvt(const CVec<From> &v)
+{
+    CVec<To> o;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        o.re[c] = To(v.re[c]);
+        o.im[c] = To(v.im[c]);
+    }
+    return o;
+}
+
+// ------------------------------------------------------- gathered links
+// For every output parity p and output site cb the 16 hop matrices W_h are
+// stored with the staggered phase, the boundary sign, the minus sign of the
+// backward hops and the adjoint of the backward links folded in, so that
+//   (D psi)(x) = sum_mu sum_{kind} [ W_fwd psi(x + n mu) + W_bwd psi(x - n mu) ]
+// (kind 0: fat, n = 1; kind 1: long, n = 3).
+//
+// FP64 (recon 18): double2 [p][mu][kind][fwd,bwd][k=0..8][Vh]
+// FP32 (recon 18): float4  [p][mu][kind][k=0..8][Vh], float4 = (fwd_k, bwd_k)
+// FP32 long links with recon 12: float4 [p][mu][k=0..5][Vh] holding rows 0,1
+//   of the SU(3) factor S of fwd and bwd; W = sign * long_scale * S, with
+//   sign = +-eta_mu(x) * (boundary sign) recomputed from the coordinates.
+struct LinksD {
+    const double2 *base; // parity offset applied
+    int Vh;
+    typedef double real;
+    __device__ __forceinline__ void load(int mu, int kind, int i, CMat<double> &f, CMat<double> &b) const
+    {
+        const double2 *q = base + size_t((mu * 2 + kind) * 2) * 9 * Vh + i;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            double2 a = __ldcs(q + size_t(k) * Vh);
+            double2 c = __ldcs(q + size_t(9 + k) * Vh);
+            f.re[k] = a.x;
+            f.im[k] = a.y;
+            b.re[k] = c.x;
+            b.im[k] = c.y;
+        }
+    }
+};
+
+struct LinksF {
+    const float4 *base; // parity offset applied
+    int Vh;
+    typedef float real;
+    __device__ __forceinline__ void load(int mu, int kind, int i, CMat<float> &f, CMat<float> &b) const
+    {
+        const float4 *q = base + size_t((mu * 2 + kind) * 9) * Vh + i;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            float4 a = __ldcs(q + size_t(k) * Vh);
+            f.re[k] = a.x;
+            f.im[k] = a.y;
+            b.re[k] = a.z;
+            b.im[k] = a.w;
+        }
+    }
+};
+
+struct LinksF12 { // long links only
+    const float4 *base; // parity offset applied
+    int Vh;
+    __device__ __forceinline__ void load(int mu, int i, CMat<float> &f, CMat<float> &b) const
+    {
+        const float4 *q = base + size_t(mu * 6) * Vh + i;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            float4 a = __ldcs(q + size_t(k) * Vh);
+            f.re[k] = a.x;
+            f.im[k] = a.y;
+            b.re[k] = a.z;
+            b.im[k] = a.w;
+        }
+        su3_third_row(f);
+        su3_third_row(b);
+    }
+};
+
+// ------------------------------------------------------ device scalars
+// Scalars of the CG recurrences live on the device so that consecutive kernels
+// of one iteration never wait for the host.
+struct DevScalars {
+    double rr;      // |r|^2 of the current iterate
+    double rr_new;  // |r|^2 after the update
+    double pp;      // |p|^2
+    double tt;      // |D_oe p|^2
+    double alpha, beta;
+    double m4;      // 4 m^2
+    double pad0;
+    long long iter; // iterations done
+    long long pad1;
+    double slot[16]; // generic reduction results
+};
+
+enum FinishOp : int {
+    FIN_STORE = 0,    // slot[i] = total_i
+    FIN_CG_ALPHA = 1, // tt = total_0; alpha = rr / (m4 pp + tt)
+    FIN_CG_BETA = 2,  // rr_new = total_0; beta = rr_new / rr; monitor[iter] = rr_new
+    FIN_CG_P = 3      // pp = total_0; rr = rr_new; iter += 1
+};
+
+constexpr int kMaxRedVals = 8;
+constexpr int kRedThreads = 256;
+
+struct RedArgs {
+    double *partials;       // >= gridDim.x * nvals doubles
+    unsigned int *ticket;   // zero between uses
+    DevScalars *scal;
+    double *monitor;        // host-mapped residual history (FIN_CG_BETA)
+    int monitor_len;
+    int op;
+    int slot0;              // first slot for FIN_STORE
+};
+
+// Deterministic grid reduction of NV doubles: each block writes its partial
+// sums, the last block to finish adds the partials in block order.
+template <int NV>
+__device__ __forceinline__ void grid_reduce(double (&v)[NV], const RedArgs &ra)
+{
+    __shared__ double sh[NV][32];
+    __shared__ bool am_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; j++) {
+        double x = v[j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) sh[j][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; j++) {
+            double s = 0;
+            for (int w = 0; w < nwarps; w++) s += sh[j][w];
+            ra.partials[size_t(blockIdx.x) * NV + j] = s;
+        }
+        __threadfence();
+        unsigned int t = atomicAdd(ra.ticket, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double tot[NV];
+#pragma unroll
+    for (int j = 0; j < NV; j++) {
+        double s = 0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+            s += ((volatile double *)ra.partials)[size_t(b) * NV + j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[j][warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; j++) {
+            double s = 0;
+            for (int w = 0; w < nwarps; w++) s += sh[j][w];
+            tot[j] = s;
+        }
+        DevScalars *S = ra.scal;
+        switch (ra.op) {
+        case FIN_STORE:
+#pragma unroll
+            for (int j = 0; j < NV; j++) S->slot[ra.slot0 + j] = tot[j];
+            break;
+        case FIN_CG_ALPHA:
+            S->tt = tot[0];
+            S->alpha = S->rr / (S->m4 * S->pp + tot[0]);
+            break;
+        case FIN_CG_BETA:
+            S->rr_new = tot[0];
+            S->beta = tot[0] / S->rr;
+            if (ra.monitor) ra.monitor[S->iter % ra.monitor_len] = tot[0];
+            break;
+        case FIN_CG_P:
+            S->pp = tot[0];
+            S->rr = S->rr_new;
+            S->iter += 1;
+            break;
+        }
+        *ra.ticket = 0u;
+        __threadfence();
+    }
+}
+
+// ---------------------------------------------------------------- context
+// persistent scratch buffers of a context, grown on demand
+enum BufId : int {
+    BUF_DEFL_PART = 0, // deflation projection partial sums
+    BUF_DEFL_C,        // deflation coefficients (complex FP64)
+    BUF_ETA_FULL,      // full-lattice FP64 source (host API)
+    BUF_PSI_FULL,      // full-lattice FP64 solution (host API)
+    BUF_ETA_E,
+    BUF_ETA_O,
+    BUF_Y,             // even-site right-hand side y_e
+    BUF_XHI,           // FP64 solution accumulator
+    BUF_RHI,           // FP64 true residual
+    BUF_TMPHI,         // FP64 odd temporary
+    BUF_PSI_O,
+    BUF_XSL,           // sloppy solution increment
+    BUF_RSL,
+    BUF_P,
+    BUF_TMP,           // sloppy odd temporary
+    BUF_TEST_A,
+    BUF_TEST_B,
+    BUF_TEST_C,
+    BUF_EPS,           // eigenvalues on the device (FP64)
+    BUF_EIG_Y,         // Ritz rotation matrix (FP64)
+    BUF_EIG_W,         // eigensolver work vectors
+    BUF_COUNT
+};
+
+struct EigenStore {
+    int n = 0;            // stored eigenpairs
+    int prec = 32;        // storage precision (32 or 16)
+    void *vecs = nullptr; // n vectors of spinor_bytes(prec, Vh)
+    std::vector<double> eps; // massless eigenvalues, ascending
+};
+
+} // namespace hisq
+
+struct hisq_ctx {
+    hisq::Geom g;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    std::string err;
+    double mass = -1;
+    bool links_loaded = false;
+    int long_recon = 18;
+    double long_scale = 1.0;
+
+    // gathered links; index [parity]
+    double2 *links_d[2] = {nullptr, nullptr};  // FP64, 16 hops
+    float4 *links_f[2] = {nullptr, nullptr};   // FP32: fat (+ long when recon 18)
+    float4 *links_f12[2] = {nullptr, nullptr}; // FP32 long, recon 12
+
+    // reduction scratch
+    double *partials = nullptr;
+    unsigned int *ticket = nullptr;
+    hisq::DevScalars *scal = nullptr;
+    double *monitor_h = nullptr; // host-mapped
+    double *monitor_d = nullptr;
+    int monitor_len = 1 << 16;
+    int max_red_blocks = 0;
+
+    hisq::EigenStore eig;
+
+    // scratch buffers (grown on demand)
+    void *bufs[hisq::BUF_COUNT] = {};
+    size_t buf_cap[hisq::BUF_COUNT] = {};
+    size_t bytes = 0;
+};
+
+namespace hisq {
+
+// error helpers (api.cu)
+hisq_status set_err(hisq_ctx *c, hisq_status s, const char *fmt, ...);
+hisq_status cuda_err(hisq_ctx *c, cudaError_t e, const char *what);
+void *dev_alloc(hisq_ctx *c, size_t bytes);
+void dev_free(hisq_ctx *c, void *p, size_t bytes);
+// persistent scratch buffer `id` of at least `bytes` (nullptr + error set on OOM)
+void *get_buf(hisq_ctx *c, int id, size_t bytes);
+
+#define HISQ_CUDA(call)                                                                  \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) return ::hisq::cuda_err(ctx, e_, #call);                  \
+    } while (0)
+
+// grid size for a grid-stride kernel over n items
+inline int grid_for(const hisq_ctx *ctx, long n, int threads, int blocks_per_sm)
+{
+    long want = (n + threads - 1) / threads;
+    long cap = long(ctx->num_sms) * blocks_per_sm;
+    if (cap > ctx->max_red_blocks) cap = ctx->max_red_blocks;
+    if (want > cap) want = cap;
+    if (want < 1) want = 1;
+    return int(want);
+}
+
+inline RedArgs red_args(hisq_ctx *ctx, int op, int slot0 = 0)
+{
+    RedArgs r;
+    r.partials = ctx->partials;
+    r.ticket = ctx->ticket;
+    r.scal = ctx->scal;
+    r.monitor = ctx->monitor_d;
+    r.monitor_len = ctx->monitor_len;
+    r.op = op;
+    r.slot0 = slot0;
+    return r;
+}
+
+// ---------------------------------------------------- launchers (kernels.cu)
+// All fields are one parity, Vh sites, in the storage format of their precision.
+// Host-layout FP64 full-lattice field <-> one parity of a device field.
+hisq_status launch_gather_parity(hisq_ctx *ctx, const double *full, int parity, int prec, void *out);
+hisq_status launch_scatter_parity(hisq_ctx *ctx, const void *in, int prec, int parity, double *full);
+// precision conversion between parity fields (also copies when equal)
+hisq_status launch_convert(hisq_ctx *ctx, const void *in, int prec_in, void *out, int prec_out);
+
+// out = a*x + b*y + c*D(in)  on output parity `out_parity`; x, y nullable,
+// all of precision `prec`, links of precision link_prec (64 or 32).
+// If norm_slot >= 0 the squared norm of out is reduced into scal->slot[norm_slot].
+hisq_status launch_dslash(hisq_ctx *ctx, int out_parity, int prec, int link_prec, const void *in,
+                          void *out, double a, const void *x, double b, const void *y, double c,
+                          int norm_slot);
+
+// CG iteration kernels (sloppy precision `prec`, links `link_prec`, x in xprec)
+hisq_status launch_cg_dslash_tt(hisq_ctx *ctx, int prec, int link_prec, const void *p, void *tmp);
+hisq_status launch_cg_dslash_update(hisq_ctx *ctx, int prec, int link_prec, int xprec,
+                                    const void *tmp, const void *p, void *x, void *r);
+hisq_status launch_cg_p_update(hisq_ctx *ctx, int prec, const void *r, void *p);
+
+// BLAS-1 on one parity
+hisq_status launch_norm2(hisq_ctx *ctx, int prec, const void *x, int slot);
+hisq_status launch_axpy_d(hisq_ctx *ctx, double a, const void *x, int xprec, double *y); // y(FP64) += a x
+hisq_status launch_zero(hisq_ctx *ctx, void *x, int prec);
+hisq_status launch_cdot(hisq_ctx *ctx, int prec, const void *x, const void *y, int slot); // <x,y> re,im
+hisq_status launch_scale_axpby_d(hisq_ctx *ctx, double a, const double *x, double b, double *y); // y = a x + b y
+
+// deflation (Eq. 4) over n stored vectors of precision vprec (32 or 16):
+// c_i = v_i^dag b (b FP64 or FP32), x += coef * sum_i d_i v_i (x FP64 or FP32)
+hisq_status launch_defl_project(hisq_ctx *ctx, int n, int vprec, const void *V, int bprec, const void *b,
+                                double *c_dev /* n complex, FP64 */);
+hisq_status launch_defl_expand(hisq_ctx *ctx, int n, int vprec, const void *V, const double *d_dev, double coef,
+                               int xprec, void *x);
+// d_i = c_i / (eps_i + shift) in place
+hisq_status launch_defl_scale(hisq_ctx *ctx, int n, double *c_dev, const double *eps_dev, double shift);
+// FP32 field helpers for the eigensolver
+hisq_status launch_scale_f(hisq_ctx *ctx, double s, const void *in, void *out);
+hisq_status launch_random_f(hisq_ctx *ctx, unsigned long long seed, void *out);
+// basis rotation for the eigensolver: out_j = sum_i Y[i][j] in_i, real Y (k_in x k_out)
+hisq_status launch_rotate(hisq_ctx *ctx, int k_in, int k_out, const void *Vin, const double *Y_dev,
+                          void *Vout);
+
+// link ingest (ingest.cu)
+hisq_status ingest_links(hisq_ctx *ctx, const double *fat_dev, const double *lng_dev, int recon,
+                         double long_scale, double *max_unitarity_err);
+
+} // namespace hisq

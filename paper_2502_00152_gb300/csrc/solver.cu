@@ -1,0 +1,338 @@
+// solver.cu -- the propagator solve of Sections 2 and 3 of the paper:
+//   y_e = (M^dag eta)_e = 2m eta_e - D_eo eta_o
+//   x_e = V Lambda^-1 V^dag y_e                       (deflated guess, Eq. 4)
+//   CG on (M^dag M)_ee x_e = y_e in sloppy precision with FP64 reliable updates
+//     (|r| < delta_rd |r_last|, delta_rd = 0.1) and re-deflation
+//     (|r| < delta_tr |r_defl|, delta_tr = 1e-3)
+//   psi_o = (eta_o - D_oe psi_e) / (2m)
+// The host drives the iterations with a one-iteration lag: it queues iteration
+// k and only then reads the residual of iteration k-1 from mapped memory, so the
+// GPU never idles waiting for the host.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace hisq {
+
+double *eig_eps_dev(hisq_ctx *ctx);
+hisq_status read_slots(hisq_ctx *ctx, int slot0, int n, double *out);
+
+#define TRY(x)                                  \
+    do {                                        \
+        hisq_status s_ = (x);                   \
+        if (s_ != HISQ_OK) return s_;           \
+    } while (0)
+
+enum Slot { SL_YNORM = 0, SL_ETAE = 1, SL_ETAO = 2, SL_RHI = 3, SL_RE = 4, SL_RO = 5, SL_PP = 6 };
+
+// r = b - A x  (FP64 operator, A = 4m^2 - D_eo D_oe), |r|^2 -> slot
+static hisq_status residual_hi(hisq_ctx *ctx, const double *b, const double *x, double *r, double *tmp_odd, int slot)
+{
+    const double m4 = 4.0 * ctx->mass * ctx->mass;
+    TRY(launch_dslash(ctx, 1, 64, 64, x, tmp_odd, 0, nullptr, 0, nullptr, 1.0, -1));
+    return launch_dslash(ctx, 0, 64, 64, tmp_odd, r, -m4, x, 1.0, b, 1.0, slot);
+}
+
+// x += V Lambda^-1 V^dag r over the first n stored eigenpairs (Eq. 4)
+hisq_status deflate_add(hisq_ctx *ctx, int n, const double *r, double *x)
+{
+    double *eps = eig_eps_dev(ctx);
+    double *c = (double *)get_buf(ctx, BUF_DEFL_C, sizeof(double) * 2 * (n > 0 ? n : 1));
+    if (!eps || !c) return set_err(ctx, HISQ_ERR_OOM, "deflation buffers");
+    TRY(launch_defl_project(ctx, n, ctx->eig.prec, ctx->eig.vecs, 64, r, c));
+    TRY(launch_defl_scale(ctx, n, c, eps, 4.0 * ctx->mass * ctx->mass));
+    return launch_defl_expand(ctx, n, ctx->eig.prec, ctx->eig.vecs, c, 1.0, 64, x);
+}
+
+struct HostScalars {
+    double rr, pp, m4;
+    long long iter;
+};
+
+static hisq_status set_scalars(hisq_ctx *ctx, const HostScalars &h)
+{
+    DevScalars s;
+    memset(&s, 0, sizeof s);
+    s.rr = h.rr;
+    s.pp = h.pp;
+    s.m4 = h.m4;
+    s.iter = h.iter;
+    HISQ_CUDA(cudaMemcpyAsync(ctx->scal, &s, offsetof(DevScalars, slot), cudaMemcpyHostToDevice, ctx->stream));
+    HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    return HISQ_OK;
+}
+
+// CG with reliable updates and re-deflation on one right-hand side.
+// b, x: FP64 even fields; x holds the initial guess on entry.
+static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const double *b, double *x, double target,
+                               int n_defl, double rn0, hisq_solve_stats *st, double *rfinal, double *defl_seconds)
+{
+    const int Vh = ctx->g.Vh;
+    const int prec = P->precision_sloppy;
+    const int lprec = prec == 64 ? 64 : 32;
+    const int xprec = prec == 64 ? 64 : 32;
+    double *r_hi = (double *)get_buf(ctx, BUF_RHI, spinor_bytes(64, Vh));
+    double *t_hi = (double *)get_buf(ctx, BUF_TMPHI, spinor_bytes(64, Vh));
+    void *x_sl = get_buf(ctx, BUF_XSL, spinor_bytes(xprec, Vh));
+    void *r_sl = get_buf(ctx, BUF_RSL, spinor_bytes(prec, Vh));
+    void *p = get_buf(ctx, BUF_P, spinor_bytes(prec, Vh));
+    void *tmp = get_buf(ctx, BUF_TMP, spinor_bytes(prec, Vh));
+    if (!r_hi || !t_hi || !x_sl || !r_sl || !p || !tmp) return HISQ_ERR_OOM;
+
+    double rt = rn0; // true residual norm, r_hi holds b - A x
+    *rfinal = rt;
+    if (rt <= target) {
+        st->converged = 1;
+        return HISQ_OK;
+    }
+    const double m4 = 4.0 * ctx->mass * ctx->mass;
+    TRY(launch_convert(ctx, r_hi, 64, r_sl, prec));
+    TRY(launch_convert(ctx, r_hi, 64, p, prec));
+    TRY(launch_zero(ctx, x_sl, xprec));
+    TRY(set_scalars(ctx, HostScalars{rt * rt, rt * rt, m4, 0}));
+
+    cudaEvent_t ev[2], d0, d1;
+    HISQ_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    HISQ_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    HISQ_CUDA(cudaEventCreate(&d0));
+    HISQ_CUDA(cudaEventCreate(&d1));
+    struct Cleanup {
+        cudaEvent_t *e;
+        ~Cleanup()
+        {
+            for (int i = 0; i < 4; i++) cudaEventDestroy(e[i]);
+        }
+    };
+    cudaEvent_t all[4] = {ev[0], ev[1], d0, d1};
+    Cleanup cleanup{all};
+
+    double r_last = rt, r_defl = rt;
+    long long k = 0, checked = 0;
+    const long long maxit = P->max_iter > 0 ? P->max_iter : 1;
+    hisq_status result = HISQ_ERR_NOT_CONVERGED;
+    for (;;) {
+        bool force = false;
+        if (k < maxit) {
+            TRY(launch_cg_dslash_tt(ctx, prec, lprec, p, tmp));
+            TRY(launch_cg_dslash_update(ctx, prec, lprec, xprec, tmp, p, x_sl, r_sl));
+            TRY(launch_cg_p_update(ctx, prec, r_sl, p));
+            HISQ_CUDA(cudaEventRecord(ev[k & 1], ctx->stream));
+            k++;
+        } else {
+            force = true;
+        }
+        bool update = force;
+        const long long j = k - 2; // the iteration before the one just queued
+        if (!force && j >= checked) {
+            HISQ_CUDA(cudaEventSynchronize(ev[j & 1]));
+            const double rr = ctx->monitor_h[j % ctx->monitor_len];
+            if (!std::isfinite(rr)) {
+                cudaStreamSynchronize(ctx->stream);
+                st->iterations = int(k);
+                return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite residual at iteration %lld", j);
+            }
+            const double rn = std::sqrt(rr);
+            if (rn < target || rn < P->delta_rd * r_last) update = true;
+            checked = j + 1;
+        }
+        if (!update) continue;
+        // ---- reliable update: x_hi += x_sl; r_hi = b - A x_hi in FP64
+        HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+        TRY(launch_axpy_d(ctx, 1.0, x_sl, xprec, x));
+        TRY(residual_hi(ctx, b, x, r_hi, t_hi, SL_RHI));
+        double r2 = 0;
+        TRY(read_slots(ctx, SL_RHI, 1, &r2));
+        if (!std::isfinite(r2)) return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite true residual");
+        rt = std::sqrt(r2);
+        st->reliable_updates++;
+        checked = k;
+        if (rt <= target) {
+            result = HISQ_OK;
+            break;
+        }
+        if (force) break;
+        bool restart = false;
+        if (n_defl > 0 && P->delta_tr > 0 && rt < P->delta_tr * r_defl) {
+            HISQ_CUDA(cudaEventRecord(d0, ctx->stream));
+            TRY(deflate_add(ctx, n_defl, r_hi, x));
+            HISQ_CUDA(cudaEventRecord(d1, ctx->stream));
+            TRY(residual_hi(ctx, b, x, r_hi, t_hi, SL_RHI));
+            TRY(read_slots(ctx, SL_RHI, 1, &r2));
+            float ms = 0;
+            cudaEventElapsedTime(&ms, d0, d1);
+            *defl_seconds += ms * 1e-3;
+            rt = std::sqrt(r2);
+            r_defl = rt;
+            st->redeflations++;
+            restart = true;
+            if (rt <= target) {
+                result = HISQ_OK;
+                break;
+            }
+        }
+        TRY(launch_convert(ctx, r_hi, 64, r_sl, prec));
+        TRY(launch_zero(ctx, x_sl, xprec));
+        double pp = -1;
+        if (restart) {
+            TRY(launch_convert(ctx, r_hi, 64, p, prec));
+            pp = rt * rt;
+        } else {
+            TRY(launch_norm2(ctx, prec, p, SL_PP));
+            TRY(read_slots(ctx, SL_PP, 1, &pp));
+        }
+        TRY(set_scalars(ctx, HostScalars{rt * rt, pp, m4, k}));
+        r_last = rt;
+    }
+    HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    st->iterations = int(k);
+    st->converged = result == HISQ_OK;
+    *rfinal = rt;
+    return result;
+}
+
+// Solve M psi = eta for one right-hand side; eta, psi: FP64 full-lattice device fields.
+hisq_status solve_one(hisq_ctx *ctx, const hisq_solve_params *P, const double *eta, double *psi, hisq_solve_stats *st)
+{
+    const int Vh = ctx->g.Vh;
+    const double m = ctx->mass;
+    memset(st, 0, sizeof *st);
+    st->full_residual = -1;
+    auto t0 = std::chrono::steady_clock::now();
+    double *eta_e = (double *)get_buf(ctx, BUF_ETA_E, spinor_bytes(64, Vh));
+    double *eta_o = (double *)get_buf(ctx, BUF_ETA_O, spinor_bytes(64, Vh));
+    double *y = (double *)get_buf(ctx, BUF_Y, spinor_bytes(64, Vh));
+    double *x = (double *)get_buf(ctx, BUF_XHI, spinor_bytes(64, Vh));
+    double *r_hi = (double *)get_buf(ctx, BUF_RHI, spinor_bytes(64, Vh));
+    double *t_hi = (double *)get_buf(ctx, BUF_TMPHI, spinor_bytes(64, Vh));
+    double *psi_o = (double *)get_buf(ctx, BUF_PSI_O, spinor_bytes(64, Vh));
+    if (!eta_e || !eta_o || !y || !x || !r_hi || !t_hi || !psi_o) return HISQ_ERR_OOM;
+
+    // (a2) source preparation
+    TRY(launch_gather_parity(ctx, eta, 0, 64, eta_e));
+    TRY(launch_gather_parity(ctx, eta, 1, 64, eta_o));
+    TRY(launch_norm2(ctx, 64, eta_e, SL_ETAE));
+    TRY(launch_norm2(ctx, 64, eta_o, SL_ETAO));
+    TRY(launch_dslash(ctx, 0, 64, 64, eta_o, y, 2.0 * m, eta_e, 0, nullptr, -1.0, SL_YNORM));
+    double nrm[3];
+    TRY(read_slots(ctx, SL_YNORM, 3, nrm));
+    const double ynorm = std::sqrt(nrm[0]), etanorm = std::sqrt(nrm[1] + nrm[2]);
+    if (!std::isfinite(ynorm) || !std::isfinite(etanorm)) return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite source");
+    HISQ_CUDA(cudaMemsetAsync(x, 0, spinor_bytes(64, Vh), ctx->stream));
+    if (etanorm == 0) {
+        HISQ_CUDA(cudaMemsetAsync(psi, 0, size_t(ctx->g.V) * 48, ctx->stream));
+        HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+        st->converged = 1;
+        st->full_residual = 0;
+        return HISQ_OK;
+    }
+    const double target = P->tol * std::fmin(ynorm, 2.0 * m * etanorm);
+
+    // (a8) deflated initial guess
+    int n_defl = 0;
+    if (P->deflate) {
+        if (ctx->eig.n <= 0) return set_err(ctx, HISQ_ERR_STATE, "deflation requested but no eigenpairs stored");
+        n_defl = P->n_defl > 0 ? std::min(P->n_defl, ctx->eig.n) : ctx->eig.n;
+    }
+    double defl_s = 0;
+    if (n_defl > 0) {
+        auto d0 = std::chrono::steady_clock::now();
+        TRY(deflate_add(ctx, n_defl, y, x));
+        HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+        defl_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - d0).count();
+    }
+    TRY(residual_hi(ctx, y, x, r_hi, t_hi, SL_RHI));
+    double r2 = 0;
+    TRY(read_slots(ctx, SL_RHI, 1, &r2));
+
+    // (a6) CG with reliable updates
+    double rfin = 0;
+    hisq_status cst = cg_reliable(ctx, P, y, x, target, n_defl, std::sqrt(r2), st, &rfin, &defl_s);
+    if (cst != HISQ_OK && cst != HISQ_ERR_NOT_CONVERGED) return cst;
+    st->even_residual = ynorm > 0 ? rfin / ynorm : 0;
+
+    // (a9) odd reconstruction psi_o = (eta_o - D_oe psi_e) / (2m)
+    TRY(launch_dslash(ctx, 1, 64, 64, x, psi_o, 1.0 / (2.0 * m), eta_o, 0, nullptr, -1.0 / (2.0 * m), -1));
+    if (P->compute_full_residual) {
+        // r_e = eta_e - 2m psi_e - D_eo psi_o ; r_o = eta_o - 2m psi_o - D_oe psi_e
+        TRY(launch_dslash(ctx, 0, 64, 64, psi_o, r_hi, -2.0 * m, x, 1.0, eta_e, -1.0, SL_RE));
+        TRY(launch_dslash(ctx, 1, 64, 64, x, t_hi, -2.0 * m, psi_o, 1.0, eta_o, -1.0, SL_RO));
+        double rr[2];
+        TRY(read_slots(ctx, SL_RE, 2, rr));
+        st->full_residual = std::sqrt(rr[0] + rr[1]) / etanorm;
+    }
+    TRY(launch_scatter_parity(ctx, x, 64, 0, psi));
+    TRY(launch_scatter_parity(ctx, psi_o, 64, 1, psi));
+    HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    st->seconds_deflate = defl_s;
+    st->seconds_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return cst;
+}
+
+static hisq_status check_solve_args(hisq_ctx *ctx, const hisq_solve_params *P, int nrhs)
+{
+    if (!P || nrhs < 0) return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad solve arguments");
+    if (!ctx->links_loaded) return set_err(ctx, HISQ_ERR_STATE, "links not loaded");
+    if (!(ctx->mass > 0)) return set_err(ctx, HISQ_ERR_STATE, "mass not set");
+    if (P->precision_sloppy != 64 && P->precision_sloppy != 32 && P->precision_sloppy != 16)
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "precision_sloppy must be 64, 32 or 16");
+    if (!(P->tol > 0) || !(P->delta_rd > 0 && P->delta_rd < 1) || P->delta_tr < 0 || P->delta_tr >= 1)
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad tolerance / delta parameters");
+    return HISQ_OK;
+}
+
+} // namespace hisq
+
+using namespace hisq;
+
+extern "C" {
+
+hisq_status hisq_solve(hisq_ctx *ctx, const double *eta, double *psi, int nrhs, const hisq_solve_params *params,
+                       hisq_solve_stats *stats)
+{
+    if (!ctx) return HISQ_ERR_INVALID_ARG;
+    if (!eta || !psi) return set_err(ctx, HISQ_ERR_INVALID_ARG, "null field");
+    TRY(check_solve_args(ctx, params, nrhs));
+    HISQ_CUDA(cudaSetDevice(ctx->device));
+    const size_t bytes = size_t(ctx->g.V) * 48;
+    double *de = (double *)get_buf(ctx, BUF_ETA_FULL, bytes);
+    double *dp = (double *)get_buf(ctx, BUF_PSI_FULL, bytes);
+    if (!de || !dp) return HISQ_ERR_OOM;
+    hisq_status worst = HISQ_OK;
+    for (int k = 0; k < nrhs; k++) {
+        hisq_solve_stats st;
+        auto t0 = std::chrono::steady_clock::now();
+        HISQ_CUDA(cudaMemcpyAsync(de, eta + size_t(k) * ctx->g.V * 6, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        hisq_status s = solve_one(ctx, params, de, dp, &st);
+        if (s != HISQ_OK && s != HISQ_ERR_NOT_CONVERGED) return s;
+        HISQ_CUDA(cudaMemcpyAsync(psi + size_t(k) * ctx->g.V * 6, dp, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+        st.seconds_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        if (stats) stats[k] = st;
+        if (s != HISQ_OK) worst = s;
+    }
+    if (worst != HISQ_OK) set_err(ctx, worst, "at least one right-hand side did not converge");
+    return worst;
+}
+
+hisq_status hisq_solve_device(hisq_ctx *ctx, const double *eta_dev, double *psi_dev, int nrhs,
+                              const hisq_solve_params *params, hisq_solve_stats *stats)
+{
+    if (!ctx) return HISQ_ERR_INVALID_ARG;
+    if (!eta_dev || !psi_dev) return set_err(ctx, HISQ_ERR_INVALID_ARG, "null field");
+    TRY(check_solve_args(ctx, params, nrhs));
+    HISQ_CUDA(cudaSetDevice(ctx->device));
+    hisq_status worst = HISQ_OK;
+    for (int k = 0; k < nrhs; k++) {
+        hisq_solve_stats st;
+        hisq_status s = solve_one(ctx, params, eta_dev + size_t(k) * ctx->g.V * 6, psi_dev + size_t(k) * ctx->g.V * 6, &st);
+        if (s != HISQ_OK && s != HISQ_ERR_NOT_CONVERGED) return s;
+        if (stats) stats[k] = st;
+        if (s != HISQ_OK) worst = s;
+    }
+    if (worst != HISQ_OK) set_err(ctx, worst, "at least one right-hand side did not converge");
+    return worst;
+}
+
+} // extern "C"

@@ -1,0 +1,295 @@
+"""Thin Python binding of the C ABI in include/hisq.h (argument marshalling only).
+
+Every function has the name of the C entry point it calls.  Host fields are
+numpy complex128 arrays shaped (V, 3) (or (nrhs, V, 3)) in the layout
+s = x + X*(y + Y*(z + Z*t)); links are complex128 arrays shaped (V, 4, 3, 3).
+Device variants take torch CUDA tensors (complex128 or float64 views of the same
+layout) and run on the context's stream.
+
+There is no fallback: if libhisq.so is missing or fails to load, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhisq.so")
+
+HISQ_OK = 0
+HISQ_ERR_INVALID_ARG = 1
+HISQ_ERR_CUDA = 2
+HISQ_ERR_OOM = 3
+HISQ_ERR_NOT_CONVERGED = 4
+HISQ_ERR_NUMERICAL = 5
+HISQ_ERR_TIMEOUT = 6
+HISQ_ERR_STATE = 7
+
+
+class HisqError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"hisq status {status}: {message}")
+        self.status = status
+
+
+class hisq_solve_params(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision_sloppy", ctypes.c_int),
+                ("link_precision_sloppy", ctypes.c_int), ("delta_rd", ctypes.c_double), ("deflate", ctypes.c_int),
+                ("n_defl", ctypes.c_int), ("delta_tr", ctypes.c_double), ("compute_full_residual", ctypes.c_int)]
+
+
+class hisq_solve_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("redeflations", ctypes.c_int),
+                ("converged", ctypes.c_int), ("even_residual", ctypes.c_double), ("full_residual", ctypes.c_double),
+                ("seconds_total", ctypes.c_double), ("seconds_deflate", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hisq_eig_params(ctypes.Structure):
+    _fields_ = [("n_ev", ctypes.c_int), ("n_kr", ctypes.c_int), ("n_keep", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_restarts", ctypes.c_int), ("cheby_degree", ctypes.c_int), ("a_min", ctypes.c_double),
+                ("a_max", ctypes.c_double), ("storage_precision", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+_lib = None
+_DP = ctypes.POINTER(ctypes.c_double)
+_VP = ctypes.c_void_p
+_CTX = ctypes.c_void_p
+
+# (name, restype, argtypes) of every entry point in include/hisq.h
+_PROTOS = [
+    ("hisq_default_solve_params", None, [ctypes.POINTER(hisq_solve_params)]),
+    ("hisq_default_eig_params", None, [ctypes.POINTER(hisq_eig_params)]),
+    ("hisq_create", ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int, _VP,
+                                   ctypes.POINTER(_CTX)]),
+    ("hisq_destroy", None, [_CTX]),
+    ("hisq_last_error", ctypes.c_char_p, [_CTX]),
+    ("hisq_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("hisq_load_links", ctypes.c_int, [_CTX, _DP, _DP, ctypes.c_int, ctypes.c_double]),
+    ("hisq_set_mass", ctypes.c_int, [_CTX, ctypes.c_double]),
+    ("hisq_apply_dslash", ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, _DP, _DP]),
+    ("hisq_apply_normal_op", ctypes.c_int, [_CTX, ctypes.c_int, _DP, _DP]),
+    ("hisq_solve", ctypes.c_int, [_CTX, _DP, _DP, ctypes.c_int, ctypes.POINTER(hisq_solve_params),
+                                  ctypes.POINTER(hisq_solve_stats)]),
+    ("hisq_solve_device", ctypes.c_int, [_CTX, _VP, _VP, ctypes.c_int, ctypes.POINTER(hisq_solve_params),
+                                         ctypes.POINTER(hisq_solve_stats)]),
+    ("hisq_eigensolve", ctypes.c_int, [_CTX, ctypes.POINTER(hisq_eig_params), ctypes.POINTER(ctypes.c_int), _DP]),
+    ("hisq_get_eigvals", ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int), _DP]),
+    ("hisq_get_eigvec", ctypes.c_int, [_CTX, ctypes.c_int, _DP]),
+    ("hisq_set_eigvecs", ctypes.c_int, [_CTX, ctypes.c_int, _DP, _DP, ctypes.c_int]),
+    ("hisq_deflate", ctypes.c_int, [_CTX, ctypes.c_int, _DP, _DP]),
+    ("hisq_save_eigvecs", ctypes.c_int, [_CTX, ctypes.c_char_p]),
+    ("hisq_load_eigvecs", ctypes.c_int, [_CTX, ctypes.c_char_p]),
+    ("hisq_device_bytes", ctypes.c_size_t, [_CTX]),
+]
+
+
+def load_library(path: Optional[str] = None):
+    """Load libhisq.so (raises if it is missing: there is no CPU fallback)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library {p} is missing: run paper_2502_00152_gb300.build.build() first")
+    lib = ctypes.CDLL(p)
+    for name, res, args in _PROTOS:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(ctx, st: int, allow_not_converged: bool = False) -> int:
+    if st == HISQ_OK or (allow_not_converged and st == HISQ_ERR_NOT_CONVERGED):
+        return st
+    msg = load_library().hisq_last_error(ctx).decode() if ctx else load_library().hisq_status_string(st).decode()
+    raise HisqError(st, msg)
+
+
+def _field(a, V: int, n: int = 1) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    if a.size != n * V * 3:
+        raise ValueError(f"field has {a.size} complex entries, expected {n * V * 3}")
+    return a
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+# --------------------------------------------------------------- entry points
+def hisq_default_solve_params(**kw) -> hisq_solve_params:
+    p = hisq_solve_params()
+    load_library().hisq_default_solve_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def hisq_default_eig_params(**kw) -> hisq_eig_params:
+    p = hisq_eig_params()
+    load_library().hisq_default_eig_params(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """Owns one hisq_ctx (destroyed on close / garbage collection)."""
+
+    def __init__(self, handle, dims):
+        self.handle = handle
+        self.dims = tuple(dims)
+        self.V = int(np.prod(dims))
+
+    def close(self):
+        if self.handle:
+            load_library().hisq_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def hisq_create(dims, t_antiperiodic: bool = True, device: int = 0, cuda_stream: Optional[int] = None) -> Context:
+    lib = load_library()
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    h = _CTX()
+    st = lib.hisq_create(d, 1 if t_antiperiodic else 0, device, cuda_stream, ctypes.byref(h))
+    _check(None, st)
+    return Context(h, dims)
+
+
+def hisq_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def hisq_last_error(ctx: Context) -> str:
+    return load_library().hisq_last_error(ctx.handle).decode()
+
+
+def hisq_status_string(status: int) -> str:
+    return load_library().hisq_status_string(status).decode()
+
+
+def hisq_load_links(ctx: Context, fat, lng, long_recon: int = 18, long_scale: float = 1.0) -> None:
+    f = np.ascontiguousarray(fat, dtype=np.complex128)
+    l = np.ascontiguousarray(lng, dtype=np.complex128)
+    if f.size != ctx.V * 36 or l.size != ctx.V * 36:
+        raise ValueError("links must have V*4*3*3 complex entries")
+    _check(ctx.handle, load_library().hisq_load_links(ctx.handle, _dp(f), _dp(l), long_recon, long_scale))
+
+
+def hisq_set_mass(ctx: Context, m: float) -> None:
+    _check(ctx.handle, load_library().hisq_set_mass(ctx.handle, m))
+
+
+def hisq_apply_dslash(ctx: Context, out_parity: int, precision: int, field) -> np.ndarray:
+    a = _field(field, ctx.V)
+    out = np.zeros((ctx.V, 3), dtype=np.complex128)
+    _check(ctx.handle, load_library().hisq_apply_dslash(ctx.handle, out_parity, precision, _dp(a), _dp(out)))
+    return out
+
+
+def hisq_apply_normal_op(ctx: Context, precision: int, field) -> np.ndarray:
+    a = _field(field, ctx.V)
+    out = np.zeros((ctx.V, 3), dtype=np.complex128)
+    _check(ctx.handle, load_library().hisq_apply_normal_op(ctx.handle, precision, _dp(a), _dp(out)))
+    return out
+
+
+def hisq_solve(ctx: Context, eta, params: Optional[hisq_solve_params] = None):
+    """Solve M psi = eta for host field(s) eta ((V,3) or (nrhs,V,3)).
+    Returns (psi, [stats dicts], status)."""
+    eta = np.asarray(eta)
+    single = eta.ndim == 2
+    nrhs = 1 if single else eta.shape[0]
+    e = _field(eta, ctx.V, nrhs)
+    psi = np.zeros((nrhs, ctx.V, 3), dtype=np.complex128)
+    p = params or hisq_default_solve_params()
+    stats = (hisq_solve_stats * max(nrhs, 1))()
+    st = load_library().hisq_solve(ctx.handle, _dp(e), _dp(psi), nrhs, ctypes.byref(p), stats)
+    _check(ctx.handle, st, allow_not_converged=True)
+    out = psi[0] if single else psi
+    return out, [stats[i].as_dict() for i in range(nrhs)], st
+
+
+def hisq_solve_device(ctx: Context, eta_dev, psi_dev, nrhs: int = 1, params: Optional[hisq_solve_params] = None):
+    """As hisq_solve on torch CUDA tensors (contiguous, complex128 or float64)."""
+    for t in (eta_dev, psi_dev):
+        if not t.is_cuda or not t.is_contiguous() or t.element_size() * t.numel() != nrhs * ctx.V * 48:
+            raise ValueError("device fields must be contiguous CUDA tensors of nrhs*V*3 complex128")
+    p = params or hisq_default_solve_params()
+    stats = (hisq_solve_stats * max(nrhs, 1))()
+    st = load_library().hisq_solve_device(ctx.handle, ctypes.c_void_p(eta_dev.data_ptr()),
+                                          ctypes.c_void_p(psi_dev.data_ptr()), nrhs, ctypes.byref(p), stats)
+    _check(ctx.handle, st, allow_not_converged=True)
+    return [stats[i].as_dict() for i in range(nrhs)], st
+
+
+def hisq_eigensolve(ctx: Context, params: hisq_eig_params):
+    """Returns (eps ascending, n_conv)."""
+    eps = np.zeros(params.n_ev)
+    nc = ctypes.c_int(0)
+    _check(ctx.handle, load_library().hisq_eigensolve(ctx.handle, ctypes.byref(params), ctypes.byref(nc), _dp(eps)))
+    return eps, nc.value
+
+
+def hisq_get_eigvals(ctx: Context) -> np.ndarray:
+    n = ctypes.c_int(0)
+    _check(ctx.handle, load_library().hisq_get_eigvals(ctx.handle, ctypes.byref(n), None))
+    eps = np.zeros(max(n.value, 1))
+    _check(ctx.handle, load_library().hisq_get_eigvals(ctx.handle, ctypes.byref(n), _dp(eps)))
+    return eps[: n.value]
+
+
+def hisq_get_eigvec(ctx: Context, i: int) -> np.ndarray:
+    out = np.zeros((ctx.V, 3), dtype=np.complex128)
+    _check(ctx.handle, load_library().hisq_get_eigvec(ctx.handle, i, _dp(out)))
+    return out
+
+
+def hisq_set_eigvecs(ctx: Context, vecs, eps=None, storage_precision: int = 32) -> None:
+    v = np.asarray(vecs)
+    n = v.shape[0]
+    v = _field(v, ctx.V, n)
+    e = None if eps is None else np.ascontiguousarray(eps, dtype=np.float64)
+    _check(ctx.handle, load_library().hisq_set_eigvecs(ctx.handle, n, _dp(v), None if e is None else _dp(e),
+                                                       storage_precision))
+
+
+def hisq_deflate(ctx: Context, b, n: int = 0) -> np.ndarray:
+    bb = _field(b, ctx.V)
+    out = np.zeros((ctx.V, 3), dtype=np.complex128)
+    _check(ctx.handle, load_library().hisq_deflate(ctx.handle, n, _dp(bb), _dp(out)))
+    return out
+
+
+def hisq_save_eigvecs(ctx: Context, path: str) -> None:
+    _check(ctx.handle, load_library().hisq_save_eigvecs(ctx.handle, path.encode()))
+
+
+def hisq_load_eigvecs(ctx: Context, path: str) -> None:
+    _check(ctx.handle, load_library().hisq_load_eigvecs(ctx.handle, path.encode()))
+
+
+def hisq_device_bytes(ctx: Context) -> int:
+    return int(load_library().hisq_device_bytes(ctx.handle))
