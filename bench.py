@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark: time per right-hand side of the deflated mixed-precision HISQ
+propagator solve on one GB300, next to plain mixed-precision CG on the same GPU.
+
+Workload (synthetic stand-in for the paper's MILC ensembles, Section 2 Table 1):
+32^3 x 64 lattice, thin links exp(i 0.3 A) (seed 2), fat = 9/8 U, long = -1/24 UUU,
+antiperiodic time, m = 0.002, 256 eigenpairs of the squared massless even-site
+operator (thick-restart Lanczos, FP32 vectors), Gaussian complex sources.
+One step = one right-hand side through the whole hot path: source preparation,
+deflated initial guess (Eq. 4), sloppy CG with FP64 reliable updates and
+re-deflation (Section 3), odd reconstruction and the FP64 full residual, to
+|eta - M psi| / |eta| <= 1e-10.  Link upload and the eigensolve are setup
+(excluded from the solve time, as in the paper) and reported separately.
+
+usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs independent replicas (different sources); the
+time is the max over ranks and value = time / (right-hand sides of all ranks).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time/RHS to 1e-10 residual, deflated vs plain CG on 1 GB300; Dslash HBM GB/s"
+SOURCE_SEED = 11
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--sloppy", type=int, default=16, help="sloppy colour-vector storage: 32 or 16")
+    ap.add_argument("--recon", type=int, default=18)
+    ap.add_argument("--n-ev", type=int, default=None)
+    ap.add_argument("--n-kr", type=int, default=None)
+    ap.add_argument("--cheby", type=int, default=60)
+    ap.add_argument("--amin", type=float, default=-2.0)
+    ap.add_argument("--eig-tol", type=float, default=1e-6)
+    ap.add_argument("--eig-prec", type=int, default=32)
+    ap.add_argument("--plain-steps", type=int, default=1)
+    ap.add_argument("--cpu-iters", type=int, default=3, help="oracle CG iterations per CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "of fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for rel in ("paper_2502_00152_gb300/csrc/dslash.cu", "paper_2502_00152_gb300/csrc/internal.cuh"):
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_key: str, sites: int):
+    """dram bytes per launch of the Dslash from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "dslash_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("kernel_source_hash") != kernel_source_hash():
+            return None
+        per_site = d["dram_bytes_per_output_site"].get(kernel_key)
+        return None if per_site is None else per_site * sites
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for r in csv.reader(io.StringIO(f.read())):
+                if len(r) >= 9:
+                    rows.append([x.strip() for x in r])
+        os.unlink(self.path)
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        smax = max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def link_bytes_per_site(recon: int) -> int:
+    # 8 fat + 8 long hop matrices, FP32: 18 reals each; 12 reals for the long ones with recon 12
+    return 8 * 72 + 8 * (48 if recon == 12 else 72)
+
+
+def spinor_bytes_per_site(prec: int) -> int:
+    return {64: 48, 32: 24, 16: 16}[prec]
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2502_00152_gb300 import build as B
+
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2502_00152_gb300 import hisq as H
+    from paper_2502_00152_gb300 import inputs as I
+
+    cfg = I.lattice_config(a.config)
+    dims, m, tol = cfg["dims"], cfg["mass"], cfg["tol"]
+    V = I.volume(dims)
+    Vh = V // 2
+    n_ev = a.n_ev if a.n_ev is not None else cfg.get("n_ev", 0)
+    n_kr = a.n_kr if a.n_kr is not None else max(int(1.5 * n_ev), n_ev + 32)
+
+    t0 = time.time()
+    fat, lng = I.hisq_links(dims, cfg["seed"], cfg["eps"])
+    t_links = time.time() - t0
+    stream = torch.cuda.current_stream()
+    ctx = H.hisq_create(dims, t_antiperiodic=True, device=local, cuda_stream=stream.cuda_stream)
+    H.hisq_load_links(ctx, fat, lng, long_recon=a.recon, long_scale=I.C3_NAIK if a.recon == 12 else 1.0)
+    H.hisq_set_mass(ctx, m)
+
+    # setup: eigensolve (excluded from the solve time, reported)
+    eig = {}
+    if n_ev > 0:
+        ep = H.hisq_default_eig_params(n_ev=n_ev, n_kr=n_kr, tol=a.eig_tol, max_restarts=100, cheby_degree=a.cheby,
+                                       a_min=a.amin, a_max=0.0, storage_precision=a.eig_prec, seed=1000 + rank)
+        torch.cuda.synchronize()
+        t0 = time.time()
+        eps, nconv = H.hisq_eigensolve(ctx, ep)
+        torch.cuda.synchronize()
+        eig = dict(seconds=time.time() - t0, n_ev=n_ev, n_kr=n_kr, converged=nconv, cheby_degree=a.cheby,
+                   eps_min=float(eps[0]), eps_max=float(eps[-1]), storage=a.eig_prec)
+
+    # sources: resident in HBM before the timed region (FP64 full-lattice fields)
+    keep_links = (fat, lng) if (rank == 0 and world == 1 and not a.no_cpu_baseline) else (None, None)
+    nsrc = a.warmup + a.steps
+    srcs = [I.gaussian_source(dims, SOURCE_SEED, rank * 1000 + k) for k in range(nsrc)]
+    eta_dev = [torch.from_numpy(s).to(f"cuda:{local}") for s in srcs]
+    if keep_links[0] is None:
+        del fat, lng
+    psi_dev = torch.zeros_like(eta_dev[0])
+    prm_defl = H.hisq_default_solve_params(tol=tol, precision_sloppy=a.sloppy, deflate=1 if n_ev > 0 else 0,
+                                           compute_full_residual=1)
+    prm_plain = H.hisq_default_solve_params(tol=tol, precision_sloppy=a.sloppy, deflate=0, compute_full_residual=1)
+
+    def solve(k, prm):
+        st, status = H.hisq_solve_device(ctx, eta_dev[k], psi_dev, 1, prm)
+        if status != H.HISQ_OK:
+            raise RuntimeError(f"solve did not converge: {st}")
+        return st[0]
+
+    # plain mixed-precision CG on the same GPU (comparison, not the headline)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    plain = [solve(k % nsrc, prm_plain) for k in range(a.plain_steps)]
+    torch.cuda.synchronize()
+    plain_ms = (time.time() - t0) * 1e3 / max(1, a.plain_steps)
+
+    for k in range(a.warmup):
+        solve(k, prm_defl)
+    H.hisq_set_profiling(ctx, True)
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    l0 = H.hisq_kernel_launches(ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
+    ev0.record(stream)
+    stats = [solve(a.warmup + k, prm_defl) for k in range(a.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    launches = H.hisq_kernel_launches(ctx) - l0
+    clk = clocks.stop()
+    H.hisq_set_profiling(ctx, False)
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=f"cuda:{local}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        torch.distributed.barrier()
+    ms_per_step = elapsed_ms / a.steps
+    value = elapsed_ms / (a.steps * world)
+
+    # end to end through the host API: pinned host source -> psi on the host
+    pin_eta = torch.from_numpy(srcs[a.warmup]).pin_memory()
+    pin_psi = torch.empty_like(pin_eta).pin_memory()
+    e2e_ms = []
+    for k in range(a.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st_h, status = H.hisq_solve(ctx, pin_eta.numpy(), prm_defl)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        if status != H.HISQ_OK:
+            raise RuntimeError("host-API solve did not converge")
+
+    # Dslash roofline from the event-timed kernels of the timed solves
+    it = sum(s["profiled_iterations"] for s in stats)
+    t_oe = sum(s["seconds_dslash_oe"] for s in stats) / max(it, 1)
+    t_eo = sum(s["seconds_dslash_eo"] for s in stats) / max(it, 1)
+    sp = spinor_bytes_per_site(a.sloppy)
+    bytes_oe = Vh * (link_bytes_per_site(a.recon) + 2 * sp)
+    xb = 24  # FP32 x in the fused update
+    bytes_eo = Vh * (link_bytes_per_site(a.recon) + sp + sp + 2 * sp + 2 * xb)
+    peak, peak_src = measured_peak_hbm()
+    ach = bytes_oe / t_oe / 1e9 if t_oe > 0 else None
+    key = f"oe_s{a.sloppy}_r{a.recon}"
+    traffic = ncu_traffic(key, Vh)
+    flops_site = 1146
+    res_max = max(s["full_residual"] for s in stats)
+
+    out = {
+        "metric": METRIC,
+        "value": round(value, 4),
+        "unit": "ms/RHS",
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if a.sloppy != 64 else "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": f"HISQ {dims[0]}^3x{dims[3]}, m={m}, {n_ev} eigenpairs (FP{a.eig_prec}), deflated "
+                        f"mixed-precision CG (FP{a.sloppy} vectors, FP32 links recon {a.recon}, FP64 reliable "
+                        f"updates), 1 Gaussian RHS per step, tol {tol}",
+            "lattice": list(dims), "mass": m, "n_ev": n_ev, "sloppy_vectors": f"fp{a.sloppy}",
+            "links": f"fp32 recon {a.recon}", "l2": "inputs larger than L2 (links and eigenvectors are GBs)",
+            "parallelism": f"replicas{world}",
+        },
+        "roofline": {
+            "bound": "hbm", "achieved": None if ach is None else round(ach, 1), "peak": peak, "unit": "GB/s",
+            "frac": None if ach is None else round(ach / peak, 4), "traffic": traffic,
+            "peak_source": peak_src, "kernel": "k_dslash D_oe (tmp = D_oe p, |tmp|^2)",
+            "algorithmic_bytes_per_launch": bytes_oe, "launch_us": round(t_oe * 1e6, 2),
+            "fused_eo_kernel": {"algorithmic_bytes_per_launch": bytes_eo, "launch_us": round(t_eo * 1e6, 2),
+                                "achieved_gbs": round(bytes_eo / t_eo / 1e9, 1) if t_eo > 0 else None},
+            "dslash_gflops": round(flops_site * Vh / t_oe / 1e9, 1) if t_oe > 0 else None,
+        },
+        "e2e": {"value": round(sorted(e2e_ms)[len(e2e_ms) // 2], 4), "unit": "ms/RHS",
+                "h2d_bytes_per_step": V * 48, "d2h_bytes_per_step": V * 48},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "plain_cg_ms_per_rhs": round(plain_ms, 3),
+        "iterations_deflated": [s["iterations"] for s in stats],
+        "iterations_plain": [s["iterations"] for s in plain],
+        "reliable_updates": [s["reliable_updates"] for s in stats],
+        "redeflations": [s["redeflations"] for s in stats],
+        "true_residual_max": res_max,
+        "speedup_vs_plain_cg": round(plain_ms / value, 3) if value > 0 else None,
+        "eigensolve": eig,
+        "link_generation_s": round(t_links, 2),
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(a, dims, cfg, 1, *keep_links)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ------------------------------------------------------------ oracle timing
+def oracle_iterations(name: str):
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_plain_cg_{name}.json")
+    try:
+        with open(path) as f:
+            return int(json.load(f)["iterations"]), "oracle plain CG iteration count from tests/golden"
+    except Exception:
+        return None, "no stored oracle iteration count"
+
+
+def cpu_baseline(a, dims, cfg, samples: int = 1, fat=None, lng=None):
+    """The FP64 oracle as it stands, on the host cores: time per CG iteration on
+    the benchmark workload (a bounded sample of a.cpu_iters iterations), scaled
+    to one right-hand side by the oracle's iteration count."""
+    from oracle.oracle import Oracle, num_threads
+    from paper_2502_00152_gb300 import inputs as I
+
+    if fat is None:
+        fat, lng = I.hisq_links(dims, cfg["seed"], cfg["eps"])
+    o = Oracle(dims, fat, lng, t_antiperiodic=True)
+    eta = I.gaussian_source(dims, SOURCE_SEED, 0)
+    b = o.prepare_source(cfg["mass"], eta)
+    per_it = []
+    for _ in range(samples):
+        t0 = time.perf_counter()
+        o.cg(cfg["mass"], b, None, 1e-300, maxiter=a.cpu_iters)
+        per_it.append((time.perf_counter() - t0) / (a.cpu_iters + 2))  # + initial and final residual applies
+    n_it, src = oracle_iterations(a.config)
+    t_it = min(per_it)
+    return {"value": round(t_it * n_it * 1e3, 1) if n_it else None, "unit": "ms/RHS", "cores": num_threads(),
+            "kind": "oracle",
+            "sample": f"{a.cpu_iters} FP64 oracle CG iterations on the full {dims[0]}^3x{dims[3]} lattice "
+                      f"({t_it * 1e3:.1f} ms per iteration incl. residual applies), x {n_it} iterations "
+                      f"({src}); extrapolated, plain CG without deflation"}
+
+
+def run_reference(a):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import build as OB
+    from paper_2502_00152_gb300 import inputs as I
+
+    OB.build()
+    cfg = I.lattice_config(a.config)
+    dims = cfg["dims"]
+    fat, lng = I.hisq_links(dims, cfg["seed"], cfg["eps"])
+    for _ in range(a.warmup):
+        cpu_baseline(a, dims, cfg, 1, fat, lng)
+    vals = []
+    t0 = time.time()
+    for _ in range(a.steps):
+        vals.append(cpu_baseline(a, dims, cfg, 1, fat, lng))
+    wall = time.time() - t0
+    v = sorted(x["value"] for x in vals if x["value"] is not None)
+    value = v[len(v) // 2] if v else None
+    cb = dict(vals[-1])
+    cb["value"] = value
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms/RHS", "n_gpus": world,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(wall * 1e3 / a.steps, 1),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"HISQ {dims[0]}^3x{dims[3]}, m={cfg['mass']}, plain FP64 CG (oracle), "
+                                  f"1 Gaussian RHS per step, tol {cfg['tol']}", "lattice": list(dims)},
+           "cpu_baseline": cb,
+           "e2e": {"value": value, "unit": "ms/RHS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

@@ -92,6 +92,11 @@ typedef struct {
     double full_residual;    /* |eta - M psi| / |eta|, FP64 (if requested, else -1) */
     double seconds_total;    /* prep + deflation + CG + reconstruction             */
     double seconds_deflate;  /* initial deflation and re-deflations                */
+    /* filled only with profiling on (hisq_set_profiling): CUDA-event time of the
+       two Dslash kernels of each sloppy CG iteration, summed over iterations    */
+    double seconds_dslash_oe; /* tmp = D_oe p, |tmp|^2                          */
+    double seconds_dslash_eo; /* 4m^2 p - D_eo tmp fused with the x, r update    */
+    int profiled_iterations;
 } hisq_solve_stats;
 
 /* Parameters of the thick-restart Lanczos eigensolve (Section 2). */
@@ -102,8 +107,10 @@ typedef struct {
     double tol;              /* Ritz residual |A v - theta v| <= tol * a_max        */
     int max_restarts;
     int cheby_degree;        /* Chebyshev filter degree (0 = Lanczos on A itself)   */
-    double a_min;            /* filter window [a_min, a_max] of the massless        */
-    double a_max;            /*   operator; <= 0: estimated                         */
+    double a_min;            /* filter window [a_min, a_max] of the massless operator.
+                                a_min > 0: given; a_min = -f < 0: placed where an
+                                estimated f * n_ev eigenvalues lie below it (0: f = 2) */
+    double a_max;            /* > 0: given; <= 0: 1.1 x a power-iteration estimate  */
     int storage_precision;   /* eigenvector storage: 32 or 16                        */
     uint64_t seed;           /* start vector                                        */
 } hisq_eig_params;
@@ -188,8 +195,16 @@ hisq_status hisq_deflate(hisq_ctx *ctx, int n, const double *b, double *x);
 hisq_status hisq_save_eigvecs(hisq_ctx *ctx, const char *path);
 hisq_status hisq_load_eigvecs(hisq_ctx *ctx, const char *path);
 
+/* Turn per-kernel CUDA-event timing of the CG iterations on (1) or off (0).
+ * Events are recorded on the context's stream around the two Dslash kernels of
+ * every iteration; the sums are returned in hisq_solve_stats. */
+hisq_status hisq_set_profiling(hisq_ctx *ctx, int on);
+
 /* Device bytes held by the context. */
 size_t hisq_device_bytes(const hisq_ctx *ctx);
+
+/* Number of CUDA kernels this context has launched so far. */
+unsigned long long hisq_kernel_launches(const hisq_ctx *ctx);
 
 #ifdef __cplusplus
 }

@@ -2,6 +2,7 @@
 // memory, link ingest, the operator test entry points and the eigenpair store.
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.cuh"
@@ -9,6 +10,16 @@
 using namespace hisq;
 
 namespace hisq {
+
+int log_level()
+{
+    static int lvl = -1;
+    if (lvl < 0) {
+        const char *e = getenv("HISQ_LOG");
+        lvl = e ? atoi(e) : 0;
+    }
+    return lvl;
+}
 
 hisq_status set_err(hisq_ctx *c, hisq_status s, const char *fmt, ...)
 {
@@ -109,6 +120,8 @@ const char *hisq_status_string(hisq_status s)
 const char *hisq_last_error(const hisq_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 size_t hisq_device_bytes(const hisq_ctx *ctx) { return ctx ? ctx->bytes : 0; }
+
+unsigned long long hisq_kernel_launches(const hisq_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
 void hisq_default_solve_params(hisq_solve_params *p)
 {

@@ -376,6 +376,7 @@ hisq_status launch_defl_project(hisq_ctx *ctx, int n, int vprec, const void *V, 
     else
         k_defl_project<SpinorH, SpinorF><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, make_spinorF(bb, Vh), part, nchunks);
     LAUNCH_CHECK("defl_project");
+    ctx->launches += 2;
     k_defl_finish<<<(n + 127) / 128, 128, 0, ctx->stream>>>(n, nchunks, part, (double2 *)c_dev, nullptr, 0.0);
     LAUNCH_CHECK("defl_finish");
     return HISQ_OK;
@@ -486,6 +487,7 @@ __global__ void k_defl_scale(int n, double2 *c, const double *eps, double shift)
 
 hisq_status launch_defl_scale(hisq_ctx *ctx, int n, double *c_dev, const double *eps_dev, double shift)
 {
+    ctx->launches++;
     k_defl_scale<<<(n + 127) / 128, 128, 0, ctx->stream>>>(n, (double2 *)c_dev, eps_dev, shift);
     LAUNCH_CHECK("defl_scale");
     return HISQ_OK;
@@ -561,6 +563,7 @@ hisq_status launch_rotate(hisq_ctx *ctx, int k_in, int k_out, const void *Vin, c
     const int Lf = 6 * ctx->g.Vh;
     const size_t ld = size_t(ctx->g.Vh) * 6; // floats between vectors (24 B per site)
     dim3 grid((Lf + RBM - 1) / RBM, (k_out + RBN - 1) / RBN);
+    ctx->launches++;
     k_rotate<<<grid, 256, 0, ctx->stream>>>(Lf, k_in, k_out, (const float *)Vin, ld, Y_dev, (float *)Vout);
     LAUNCH_CHECK("rotate");
     return HISQ_OK;

@@ -314,35 +314,25 @@ static hisq_status trlm(hisq_ctx *ctx, const hisq_eig_params *P, int *n_conv, do
         }
         amax = 1.1 * lam + 0.1;
     }
-    if (deg > 0 && !(amin > 0)) return set_err(ctx, HISQ_ERR_INVALID_ARG, "a_min must be given with a Chebyshev filter");
-    if (deg > 0 && !(amin < amax)) return set_err(ctx, HISQ_ERR_INVALID_ARG, "need a_min < a_max");
-    const bool want_largest = deg > 0;
-    auto op = [&](const void *v, void *out) -> hisq_status {
-        return deg > 0 ? op_cheby(ctx, W, deg, amin, amax, v, out) : op_A0(ctx, W, v, out);
-    };
-
-    // start vector
-    TRY(launch_random_f(ctx, P->seed, vec(0)));
-    {
+    std::vector<double> alpha(n_kr, 0.0), beta(n_kr, 0.0), theta_keep, s_keep;
+    std::vector<double> coefh(2 * (n_kr + 1));
+    auto start = [&](uint64_t seed) -> hisq_status {
+        TRY(launch_random_f(ctx, seed, vec(0)));
         TRY(launch_norm2(ctx, 32, vec(0), ESL_A));
         double nn;
         TRY(read_slots(ctx, ESL_A, 1, &nn));
-        TRY(launch_scale_f(ctx, 1.0 / std::sqrt(nn), vec(0), vec(0)));
-    }
-    std::vector<double> alpha(n_kr, 0.0), beta(n_kr, 0.0), theta_keep, s_keep;
-    int k = 0; // kept vectors
-    int conv = 0;
-    std::vector<double> ritz, Y;
-    std::vector<double> coefh(2 * (n_kr + 1));
-    for (int restart = 0; restart <= P->max_restarts; restart++) {
-        for (int j = k; j < n_kr; j++) {
-            TRY(op(vec(j), w));
-            // classical Gram-Schmidt against v_0..v_j, twice
+        return launch_scale_f(ctx, 1.0 / std::sqrt(nn), vec(0), vec(0));
+    };
+    // Lanczos steps j0 .. j1-1 with full reorthogonalisation (classical
+    // Gram-Schmidt against v_0..v_j, twice): alpha_j, beta_j, v_{j+1}
+    auto lanczos = [&](int j0, int j1, bool filtered) -> hisq_status {
+        for (int j = j0; j < j1; j++) {
+            TRY(filtered ? op_cheby(ctx, W, deg, amin, amax, vec(j), w) : op_A0(ctx, W, vec(j), w));
             for (int pass = 0; pass < 2; pass++) {
                 TRY(launch_defl_project(ctx, j + 1, 32, B, 32, w, coef));
-                if (pass == 0) {
-                    HISQ_CUDA(cudaMemcpyAsync(coefh.data(), coef, sizeof(double) * 2 * (j + 1), cudaMemcpyDeviceToHost, ctx->stream));
-                }
+                if (pass == 0)
+                    HISQ_CUDA(cudaMemcpyAsync(coefh.data(), coef, sizeof(double) * 2 * (j + 1), cudaMemcpyDeviceToHost,
+                                              ctx->stream));
                 TRY(launch_defl_expand(ctx, j + 1, 32, B, coef, -1.0, 32, w));
             }
             TRY(launch_norm2(ctx, 32, w, ESL_A));
@@ -354,6 +344,48 @@ static hisq_status trlm(hisq_ctx *ctx, const hisq_eig_params *P, int *n_conv, do
             if (beta[j] < 1e-30) beta[j] = 1e-30;
             TRY(launch_scale_f(ctx, 1.0 / beta[j], w, vec(j + 1)));
         }
+        return HISQ_OK;
+    };
+    if (deg > 0 && !(amin > 0)) {
+        // Window edge from a stochastic Lanczos quadrature estimate of the
+        // eigenvalue count (Lin, Saad & Yang, SIAM Review 58 (2016) 34): m plain
+        // Lanczos steps from a random vector give nodes theta_j with weights
+        // tau_j^2 (first components of the Ritz vectors), and the number of
+        // eigenvalues below x is about dim * sum_{theta_j <= x} tau_j^2.
+        const double want = (amin < 0 ? -amin : 2.0) * n_ev;
+        const int m = std::min(n_kr, std::min(dim - 1, 256));
+        TRY(start(P->seed ^ 0x9e3779b97f4a7c15ull));
+        TRY(lanczos(0, m, false));
+        std::vector<double> T(size_t(m) * m, 0.0), th, Z;
+        for (int j = 0; j < m; j++) {
+            T[size_t(j) * m + j] = alpha[j];
+            if (j + 1 < m) T[size_t(j) * m + j + 1] = T[size_t(j + 1) * m + j] = beta[j];
+        }
+        sym_eig(m, T, th, Z);
+        double cum = 0;
+        amin = th[m - 1];
+        for (int j = 0; j < m; j++) {
+            cum += Z[j] * Z[j]; // row 0, column j
+            if (double(dim) * cum >= want) {
+                amin = th[j];
+                break;
+            }
+        }
+        if (!(amin < amax)) amin = 0.5 * amax;
+    }
+    if (deg > 0 && !(amin > 0 && amin < amax)) return set_err(ctx, HISQ_ERR_INVALID_ARG, "need 0 < a_min < a_max");
+    if (log_level() > 0) fprintf(stderr, "[hisq] trlm: degree %d, window [%.6g, %.6g]\n", deg, amin, amax);
+    ctx->last_window[0] = amin;
+    ctx->last_window[1] = amax;
+    const bool want_largest = deg > 0;
+
+    // start vector
+    TRY(start(P->seed));
+    int k = 0; // kept vectors
+    int conv = 0;
+    std::vector<double> ritz, Y;
+    for (int restart = 0; restart <= P->max_restarts; restart++) {
+        TRY(lanczos(k, n_kr, deg > 0));
         // Rayleigh-Ritz on the n_kr x n_kr arrowhead + tridiagonal matrix
         std::vector<double> T(size_t(n_kr) * n_kr, 0.0);
         for (int i = 0; i < k; i++) {
@@ -380,6 +412,9 @@ static hisq_status trlm(hisq_ctx *ctx, const hisq_eig_params *P, int *n_conv, do
             else break;
         }
         const bool done = conv >= n_ev || restart == P->max_restarts;
+        if (log_level() > 0)
+            fprintf(stderr, "[hisq] trlm restart %d: %d/%d converged, window [%.4g, %.4g], ritz %.6g .. %.6g\n",
+                    restart, conv, n_ev, amin, amax, th[order[0]], th[order[n_ev - 1]]);
         const int nout = done ? n_ev : n_keep;
         Y.assign(size_t(n_kr) * nout, 0.0);
         for (int r = 0; r < n_kr; r++)

@@ -151,6 +151,7 @@ hisq_status ingest_links(hisq_ctx *ctx, const double *fat_dev, const double *lng
         IngestOut o{ctx->links_d[par], ctx->links_f[par], recon == 12 ? ctx->links_f12[par] : nullptr, nk};
         int grid = (4 * Vh + 255) / 256;
         if (grid > ctx->num_sms * 16) grid = ctx->num_sms * 16;
+        ctx->launches++;
         k_ingest<<<grid, 256, 0, ctx->stream>>>(ctx->g, par, (const double2 *)fat_dev, (const double2 *)lng_dev, o,
                                                 1.0 / long_scale, recon, d_dev, d_bad);
         cudaError_t e = cudaGetLastError();

@@ -488,6 +488,9 @@ struct hisq_ctx {
     std::string err;
     double mass = -1;
     bool links_loaded = false;
+    bool profile = false;
+    mutable unsigned long long launches = 0; // kernels launched by this context
+    double last_window[2] = {0, 0}; // Chebyshev window of the last eigensolve
     int long_recon = 18;
     double long_scale = 1.0;
 
@@ -515,6 +518,9 @@ struct hisq_ctx {
 
 namespace hisq {
 
+// verbosity from the HISQ_LOG environment variable (0 = silent)
+int log_level();
+
 // error helpers (api.cu)
 hisq_status set_err(hisq_ctx *c, hisq_status s, const char *fmt, ...);
 hisq_status cuda_err(hisq_ctx *c, cudaError_t e, const char *what);
@@ -532,6 +538,7 @@ void *get_buf(hisq_ctx *c, int id, size_t bytes);
 // grid size for a grid-stride kernel over n items
 inline int grid_for(const hisq_ctx *ctx, long n, int threads, int blocks_per_sm)
 {
+    ctx->launches++; // every grid-stride launch sizes its grid here
     long want = (n + threads - 1) / threads;
     long cap = long(ctx->num_sms) * blocks_per_sm;
     if (cap > ctx->max_red_blocks) cap = ctx->max_red_blocks;

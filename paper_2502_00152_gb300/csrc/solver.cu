@@ -107,6 +107,34 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
     };
     cudaEvent_t all[4] = {ev[0], ev[1], d0, d1};
     Cleanup cleanup{all};
+    // optional kernel timing: ring of 4 iterations x 3 events
+    const bool prof = ctx->profile;
+    cudaEvent_t pe[4][3] = {};
+    struct ProfFree {
+        cudaEvent_t (*e)[3];
+        ~ProfFree()
+        {
+            for (int i = 0; i < 4; i++)
+                for (int j = 0; j < 3; j++)
+                    if (e[i][j]) cudaEventDestroy(e[i][j]);
+        }
+    } prof_free{pe};
+    if (prof)
+        for (int i = 0; i < 4; i++)
+            for (int j = 0; j < 3; j++) HISQ_CUDA(cudaEventCreate(&pe[i][j]));
+    long long retired = 0;
+    auto retire = [&](long long n_done) {
+        if (!prof) return;
+        for (; retired < n_done; retired++) {
+            float a = 0, b = 0;
+            cudaEvent_t *e = pe[retired & 3];
+            if (cudaEventElapsedTime(&a, e[0], e[1]) == cudaSuccess && cudaEventElapsedTime(&b, e[1], e[2]) == cudaSuccess) {
+                st->seconds_dslash_oe += a * 1e-3;
+                st->seconds_dslash_eo += b * 1e-3;
+                st->profiled_iterations++;
+            }
+        }
+    };
 
     double r_last = rt, r_defl = rt;
     long long k = 0, checked = 0;
@@ -115,8 +143,11 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
     for (;;) {
         bool force = false;
         if (k < maxit) {
+            if (prof) HISQ_CUDA(cudaEventRecord(pe[k & 3][0], ctx->stream));
             TRY(launch_cg_dslash_tt(ctx, prec, lprec, p, tmp));
+            if (prof) HISQ_CUDA(cudaEventRecord(pe[k & 3][1], ctx->stream));
             TRY(launch_cg_dslash_update(ctx, prec, lprec, xprec, tmp, p, x_sl, r_sl));
+            if (prof) HISQ_CUDA(cudaEventRecord(pe[k & 3][2], ctx->stream));
             TRY(launch_cg_p_update(ctx, prec, r_sl, p));
             HISQ_CUDA(cudaEventRecord(ev[k & 1], ctx->stream));
             k++;
@@ -136,10 +167,12 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
             const double rn = std::sqrt(rr);
             if (rn < target || rn < P->delta_rd * r_last) update = true;
             checked = j + 1;
+            retire(j + 1);
         }
         if (!update) continue;
         // ---- reliable update: x_hi += x_sl; r_hi = b - A x_hi in FP64
         HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+        retire(k);
         TRY(launch_axpy_d(ctx, 1.0, x_sl, xprec, x));
         TRY(residual_hi(ctx, b, x, r_hi, t_hi, SL_RHI));
         double r2 = 0;
@@ -148,6 +181,8 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
         rt = std::sqrt(r2);
         st->reliable_updates++;
         checked = k;
+        if (log_level() > 0)
+            fprintf(stderr, "[hisq] cg it %lld: reliable update, true |r| %.4e (target %.4e)\n", k, rt, target);
         if (rt <= target) {
             result = HISQ_OK;
             break;
@@ -186,6 +221,7 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
         r_last = rt;
     }
     HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    retire(k);
     st->iterations = int(k);
     st->converged = result == HISQ_OK;
     *rfinal = rt;
@@ -314,6 +350,13 @@ hisq_status hisq_solve(hisq_ctx *ctx, const double *eta, double *psi, int nrhs, 
     }
     if (worst != HISQ_OK) set_err(ctx, worst, "at least one right-hand side did not converge");
     return worst;
+}
+
+hisq_status hisq_set_profiling(hisq_ctx *ctx, int on)
+{
+    if (!ctx) return HISQ_ERR_INVALID_ARG;
+    ctx->profile = on != 0;
+    return HISQ_OK;
 }
 
 hisq_status hisq_solve_device(hisq_ctx *ctx, const double *eta_dev, double *psi_dev, int nrhs,

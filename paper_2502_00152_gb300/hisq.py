@@ -45,7 +45,9 @@ class hisq_solve_params(ctypes.Structure):
 class hisq_solve_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("redeflations", ctypes.c_int),
                 ("converged", ctypes.c_int), ("even_residual", ctypes.c_double), ("full_residual", ctypes.c_double),
-                ("seconds_total", ctypes.c_double), ("seconds_deflate", ctypes.c_double)]
+                ("seconds_total", ctypes.c_double), ("seconds_deflate", ctypes.c_double),
+                ("seconds_dslash_oe", ctypes.c_double), ("seconds_dslash_eo", ctypes.c_double),
+                ("profiled_iterations", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -86,7 +88,9 @@ _PROTOS = [
     ("hisq_deflate", ctypes.c_int, [_CTX, ctypes.c_int, _DP, _DP]),
     ("hisq_save_eigvecs", ctypes.c_int, [_CTX, ctypes.c_char_p]),
     ("hisq_load_eigvecs", ctypes.c_int, [_CTX, ctypes.c_char_p]),
+    ("hisq_set_profiling", ctypes.c_int, [_CTX, ctypes.c_int]),
     ("hisq_device_bytes", ctypes.c_size_t, [_CTX]),
+    ("hisq_kernel_launches", ctypes.c_ulonglong, [_CTX]),
 ]
 
 
@@ -291,5 +295,13 @@ def hisq_load_eigvecs(ctx: Context, path: str) -> None:
     _check(ctx.handle, load_library().hisq_load_eigvecs(ctx.handle, path.encode()))
 
 
+def hisq_set_profiling(ctx: Context, on: bool = True) -> None:
+    _check(ctx.handle, load_library().hisq_set_profiling(ctx.handle, 1 if on else 0))
+
+
 def hisq_device_bytes(ctx: Context) -> int:
     return int(load_library().hisq_device_bytes(ctx.handle))
+
+
+def hisq_kernel_launches(ctx: Context) -> int:
+    return int(load_library().hisq_kernel_launches(ctx.handle))

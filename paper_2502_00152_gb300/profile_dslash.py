@@ -1,0 +1,38 @@
+"""Run a few plain CG iterations on a benchmark lattice so that a profiler can
+capture the Dslash kernels in the same launch configuration as the solve.
+
+usage: python -m paper_2502_00152_gb300.profile_dslash [--config c4] [--iters 4]
+                                                      [--sloppy 16] [--recon 18]
+Kernel order of one call: source preparation and initial residual (three FP64
+Dslash launches), then per CG iteration the D_oe kernel, the fused D_eo + update
+kernel and the direction update.
+"""
+import argparse
+
+from paper_2502_00152_gb300 import hisq as H
+from paper_2502_00152_gb300 import inputs as I
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--config", default="c4")
+    ap.add_argument("--iters", type=int, default=4)
+    ap.add_argument("--sloppy", type=int, default=16)
+    ap.add_argument("--recon", type=int, default=18)
+    a = ap.parse_args()
+    c = I.lattice_config(a.config)
+    dims = c["dims"]
+    fat, lng = I.hisq_links(dims, c["seed"], c["eps"])
+    ctx = H.hisq_create(dims, t_antiperiodic=True, device=0)
+    H.hisq_load_links(ctx, fat, lng, long_recon=a.recon, long_scale=I.C3_NAIK if a.recon == 12 else 1.0)
+    H.hisq_set_mass(ctx, c["mass"])
+    eta = I.gaussian_source(dims, 11, 0)
+    prm = H.hisq_default_solve_params(tol=1e-14, max_iter=a.iters, precision_sloppy=a.sloppy,
+                                      compute_full_residual=0)
+    _, st, status = H.hisq_solve(ctx, eta, prm)
+    print(f"{a.config} {dims}: {st[0]['iterations']} iterations, status {status}")
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
