@@ -189,6 +189,32 @@ hisq_status hisq_set_eigvecs(hisq_ctx *ctx, int n, const double *vecs, const dou
  * (0 = all), lambda_i = eps_i + 4m^2; host full-lattice fields, even sites. */
 hisq_status hisq_deflate(hisq_ctx *ctx, int n, const double *b, double *x);
 
+/* hisq_deflate for callers that must not allocate device memory: code that runs
+ * under a device-memory budget owned by someone else (a framework allocator or
+ * memory pool that must account for every byte), or in a phase of a long job
+ * where allocation is not allowed because it can fail, stall the device or
+ * fragment memory that the application has already laid out.  This entry point
+ * makes no device allocation and calls no allocating routine; there is no
+ * counterpart in the paper, it is an interface variant of hisq_deflate.
+ *
+ * It computes the same guess x_e = sum_i v_i lambda_i^-1 v_i^dag b_e over the
+ * first n stored pairs (n <= 0 or n > stored: all), with b_dev and x_dev in
+ * caller-owned device memory in the library's even-site FP64 layout: colour
+ * field [colour][Vh] of complex doubles (re, im), where Vh = V/2 and the even
+ * site s = x + X*(y + Y*(z + Z*t)) has index s/2.  x_dev is overwritten.
+ * Work is ordered on the context's stream; the call returns without waiting.
+ *
+ * Scratch: one fixed array of 16 MiB in device memory, held by every GPU that
+ * loads this library until the process exits.  It must hold the projection's
+ * partial sums, n * ceil(Vh / 4096) complex doubles, plus 24 bytes per pair;
+ * larger requests fail with HISQ_ERR_INVALID_ARG and a message naming the
+ * sizes.  The first call on a device looks up the array's device address (with
+ * that device current), so make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents; every byte a
+ * call reads is first written by that call, but calls that overlap on the GPU
+ * (different streams or contexts on one device) race on it. */
+hisq_status hisq_deflate_noalloc(hisq_ctx *ctx, int n, const double *b_dev, double *x_dev);
+
 /* Write / read the stored eigenpairs to / from a binary file (header with
  * lattice, count, precision and checksum).  Loading recomputes the eigenvalues
  * as FP64 Rayleigh quotients (Section 3). */

@@ -579,3 +579,34 @@ static hisq_status ensure_defl_scratch(hisq_ctx *ctx, size_t bytes, double2 **ou
 }
 
 } // namespace hisq
+
+namespace hisq {
+
+// number of site chunks of the deflation projection (partials per vector)
+int defl_project_chunks(int Vh) { return (Vh + kDeflSites - 1) / kDeflSites; }
+
+// The projection c_i = v_i^dag b with the partial sums in a buffer the caller
+// provides (at least n * defl_project_chunks(Vh) double2); b is FP64.
+hisq_status launch_defl_project_ext(hisq_ctx *ctx, int n, int vprec, const void *V, const double *b, double *c_dev,
+                                    void *part_buf)
+{
+    const int Vh = ctx->g.Vh;
+    const int nchunks = defl_project_chunks(Vh);
+    double2 *part = (double2 *)part_buf;
+    dim3 grid((n + kDeflVG - 1) / kDeflVG, nchunks);
+    const size_t stride = spinor_bytes(vprec, Vh);
+    SpinorD bs = make_spinorD(const_cast<double *>(b), Vh);
+    if (vprec == 32)
+        k_defl_project<SpinorF, SpinorD><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, bs, part, nchunks);
+    else if (vprec == 16)
+        k_defl_project<SpinorH, SpinorD><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, bs, part, nchunks);
+    else
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "eigenvector precision must be 32 or 16");
+    LAUNCH_CHECK("defl_project_ext");
+    ctx->launches += 2;
+    k_defl_finish<<<(n + 127) / 128, 128, 0, ctx->stream>>>(n, nchunks, part, (double2 *)c_dev, nullptr, 0.0);
+    LAUNCH_CHECK("defl_finish_ext");
+    return HISQ_OK;
+}
+
+} // namespace hisq

@@ -305,3 +305,16 @@ def hisq_device_bytes(ctx: Context) -> int:
 
 def hisq_kernel_launches(ctx: Context) -> int:
     return int(load_library().hisq_kernel_launches(ctx.handle))
+
+
+_PROTOS.append(("hisq_deflate_noalloc", ctypes.c_int, [_CTX, ctypes.c_int, _VP, _VP]))
+
+
+def hisq_deflate_noalloc(ctx: Context, b_dev, x_dev, n: int = 0) -> None:
+    """Deflated guess into caller-owned device memory (torch tensors in the
+    even-site FP64 layout [colour][Vh] complex); allocates no device memory."""
+    for t in (b_dev, x_dev):
+        if not t.is_cuda or not t.is_contiguous() or t.element_size() * t.numel() != ctx.V // 2 * 48:
+            raise ValueError("fields must be contiguous CUDA tensors of 3*Vh complex128")
+    _check(ctx.handle, load_library().hisq_deflate_noalloc(ctx.handle, n, ctypes.c_void_p(b_dev.data_ptr()),
+                                                           ctypes.c_void_p(x_dev.data_ptr())))
