@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="c2")
     ap.add_argument("--sloppy", type=int, default=16, help="sloppy colour-vector storage: 32 or 16")
-    ap.add_argument("--recon", type=int, default=18)
+    ap.add_argument("--recon", type=int, default=12, help="long links: 18 reals or 12 (two rows + SU(3) row)")
+    ap.add_argument("--links", type=int, default=32, help="sloppy link storage: 32 or 16")
     ap.add_argument("--n-ev", type=int, default=None)
     ap.add_argument("--n-kr", type=int, default=None)
     ap.add_argument("--cheby", type=int, default=60)
@@ -60,6 +61,21 @@ def parse():
 
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def replica_time(elapsed_ms: float, steps: int, device="cpu"):
+    """Replicas only: every rank solves its own right-hand sides; the job time is
+    the slowest rank's and value = time / (right-hand sides of all ranks).
+    Returns (max elapsed ms, ms per RHS of the whole job)."""
+    import torch
+    import torch.distributed as dist
+
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    if world > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    return elapsed_ms, elapsed_ms / (steps * world)
 
 
 def measured_peak_hbm():
@@ -139,9 +155,10 @@ class Clocks:
                 "samples": len(rows)}
 
 
-def link_bytes_per_site(recon: int) -> int:
-    # 8 fat + 8 long hop matrices, FP32: 18 reals each; 12 reals for the long ones with recon 12
-    return 8 * 72 + 8 * (48 if recon == 12 else 72)
+def link_bytes_per_site(recon: int, link_prec: int = 32) -> int:
+    # 8 fat + 8 long hop matrices of 18 reals (12 for the long ones with recon 12)
+    rb = link_prec // 8
+    return 8 * 18 * rb + 8 * (12 if recon == 12 else 18) * rb
 
 
 def spinor_bytes_per_site(prec: int) -> int:
@@ -203,9 +220,10 @@ def run_ours(a):
     if keep_links[0] is None:
         del fat, lng
     psi_dev = torch.zeros_like(eta_dev[0])
-    prm_defl = H.hisq_default_solve_params(tol=tol, precision_sloppy=a.sloppy, deflate=1 if n_ev > 0 else 0,
-                                           compute_full_residual=1)
-    prm_plain = H.hisq_default_solve_params(tol=tol, precision_sloppy=a.sloppy, deflate=0, compute_full_residual=1)
+    prm_defl = H.hisq_default_solve_params(tol=tol, precision_sloppy=a.sloppy, link_precision_sloppy=a.links,
+                                           deflate=1 if n_ev > 0 else 0, compute_full_residual=1)
+    prm_plain = H.hisq_default_solve_params(tol=tol, precision_sloppy=a.sloppy, link_precision_sloppy=a.links,
+                                            deflate=0, compute_full_residual=1)
 
     def solve(k, prm):
         st, status = H.hisq_solve_device(ctx, eta_dev[k], psi_dev, 1, prm)
@@ -239,14 +257,10 @@ def run_ours(a):
     launches = H.hisq_kernel_launches(ctx) - l0
     clk = clocks.stop()
     H.hisq_set_profiling(ctx, False)
-    elapsed_ms = ev0.elapsed_time(ev1)
+    elapsed_ms, value = replica_time(ev0.elapsed_time(ev1), a.steps, f"cuda:{local}")
     if world > 1:
-        t = torch.tensor([elapsed_ms], device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
         torch.distributed.barrier()
     ms_per_step = elapsed_ms / a.steps
-    value = elapsed_ms / (a.steps * world)
 
     # end to end through the host API: pinned host source -> psi on the host
     pin_eta = torch.from_numpy(srcs[a.warmup]).pin_memory()
@@ -265,12 +279,13 @@ def run_ours(a):
     t_oe = sum(s["seconds_dslash_oe"] for s in stats) / max(it, 1)
     t_eo = sum(s["seconds_dslash_eo"] for s in stats) / max(it, 1)
     sp = spinor_bytes_per_site(a.sloppy)
-    bytes_oe = Vh * (link_bytes_per_site(a.recon) + 2 * sp)
+    lb = link_bytes_per_site(a.recon, a.links)
+    bytes_oe = Vh * (lb + 2 * sp)
     xb = 24  # FP32 x in the fused update
-    bytes_eo = Vh * (link_bytes_per_site(a.recon) + sp + sp + 2 * sp + 2 * xb)
+    bytes_eo = Vh * (lb + sp + sp + 2 * sp + 2 * xb)
     peak, peak_src = measured_peak_hbm()
     ach = bytes_oe / t_oe / 1e9 if t_oe > 0 else None
-    key = f"oe_s{a.sloppy}_r{a.recon}"
+    key = f"oe_s{a.sloppy}_r{a.recon}" + ("" if a.links == 32 else f"_l{a.links}")
     traffic = ncu_traffic(key, Vh)
     flops_site = 1146
     res_max = max(s["full_residual"] for s in stats)
@@ -290,10 +305,10 @@ def run_ours(a):
         "data": "synthetic",
         "config": {
             "workload": f"HISQ {dims[0]}^3x{dims[3]}, m={m}, {n_ev} eigenpairs (FP{a.eig_prec}), deflated "
-                        f"mixed-precision CG (FP{a.sloppy} vectors, FP32 links recon {a.recon}, FP64 reliable "
-                        f"updates), 1 Gaussian RHS per step, tol {tol}",
+                        f"mixed-precision CG (FP{a.sloppy} vectors, FP{a.links} links recon {a.recon}, FP64 "
+                        f"reliable updates), 1 Gaussian RHS per step, tol {tol}",
             "lattice": list(dims), "mass": m, "n_ev": n_ev, "sloppy_vectors": f"fp{a.sloppy}",
-            "links": f"fp32 recon {a.recon}", "l2": "inputs larger than L2 (links and eigenvectors are GBs)",
+            "links": f"fp{a.links} recon {a.recon}", "l2": "inputs larger than L2 (links and eigenvectors are GBs)",
             "parallelism": f"replicas{world}",
         },
         "roofline": {

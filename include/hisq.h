@@ -74,12 +74,19 @@ typedef struct {
                                 (FP64 true residual); 1e-10 in the benchmarks      */
     int max_iter;            /* sloppy CG iterations per right-hand side            */
     int precision_sloppy;    /* colour-vector storage of the sloppy CG: 64, 32, 16 */
-    int link_precision_sloppy; /* link storage of the sloppy operator: 64 or 32     */
+    int link_precision_sloppy; /* link storage of the sloppy operator: 32 or 16
+                                  (ignored, FP64, when precision_sloppy is 64)     */
     double delta_rd;         /* reliable update when |r| < delta_rd * |r_last|; 0.1 */
     int deflate;             /* 1: deflated initial guess from the stored eigenpairs */
     int n_defl;              /* eigenpairs used (<= stored); 0 = all stored         */
     double delta_tr;         /* re-deflate when |r| < delta_tr * |r_defl|; 0 = off  */
     int compute_full_residual; /* 1: also return |eta - M psi| / |eta| in FP64     */
+    int batch;               /* 1: solve the right-hand sides of one call together,
+                                up to 64 at a time (each keeps its own CG, reliable
+                                updates and re-deflations; one batched operator
+                                application per iteration reads the links once);
+                                needs precision_sloppy 32|16 and FP32 links.
+                                0: one right-hand side after the other            */
 } hisq_solve_params;
 
 /* Per right-hand-side results of a solve. */
@@ -134,7 +141,7 @@ const char *hisq_status_string(hisq_status s);
  * 12 stores two rows of long/long_scale (which must then be SU(3) to 1e-6;
  * otherwise HISQ_ERR_INVALID_ARG) and rebuilds the third row on the fly.  The
  * library folds staggered phases, boundary signs and the backward adjoints into
- * its own device copies (FP64 and FP32).  Non-finite input: HISQ_ERR_NUMERICAL. */
+ * its own device copies (FP64, FP32 and FP16).  Non-finite input: HISQ_ERR_NUMERICAL. */
 hisq_status hisq_load_links(hisq_ctx *ctx, const double *fat, const double *lng, int long_recon,
                             double long_scale);
 
@@ -143,14 +150,16 @@ hisq_status hisq_set_mass(hisq_ctx *ctx, double m);
 
 /* out_parity sites of `out` = D applied to the opposite-parity sites of `in`
  * (host full-lattice fields); the other parity of `out` is set to zero.
- * precision 64: FP64 links and vectors; 32: FP32; 16: FP16 vectors, FP32 links.
+ * precision: colour-vector storage (64, 32, 16); link_precision: link storage
+ * (64 with precision 64; 32 or 16 otherwise; arithmetic FP32).
  * Test and diagnostic entry point. */
-hisq_status hisq_apply_dslash(hisq_ctx *ctx, int out_parity, int precision, const double *in,
-                              double *out);
+hisq_status hisq_apply_dslash(hisq_ctx *ctx, int out_parity, int precision, int link_precision,
+                              const double *in, double *out);
 
 /* Even sites of `out` = (M^dag M)_ee applied to the even sites of `in`
  * (= 4m^2 in_e - D_eo D_oe in_e); odd sites of `out` are zero. */
-hisq_status hisq_apply_normal_op(hisq_ctx *ctx, int precision, const double *in, double *out);
+hisq_status hisq_apply_normal_op(hisq_ctx *ctx, int precision, int link_precision, const double *in,
+                                 double *out);
 
 /* Solve M psi_k = eta_k for nrhs right-hand sides (host full-lattice fields,
  * right-hand side k at offset k*V*6 doubles).  stats: nrhs entries (nullable).
@@ -214,6 +223,14 @@ hisq_status hisq_deflate(hisq_ctx *ctx, int n, const double *b, double *x);
  * call reads is first written by that call, but calls that overlap on the GPU
  * (different streams or contexts on one device) race on it. */
 hisq_status hisq_deflate_noalloc(hisq_ctx *ctx, int n, const double *b_dev, double *x_dev);
+
+/* Batched deflation on the tensor cores (Eq. 4 for several right-hand sides, the
+ * paper's Section 4 outlook): for nrhs <= 32 host full-lattice fields b_j,
+ * x_j = sum_i v_i lambda_i^-1 v_i^dag b_j and r_j = b_j - sum_i v_i v_i^dag b_j
+ * over the first n <= 512 stored pairs (0 = all), even sites.  Needs FP32
+ * eigenvector storage; the projection and the expansion are complex GEMMs in
+ * FP16 (split into high and low parts) with FP32 accumulation. */
+hisq_status hisq_deflate_batch(hisq_ctx *ctx, int n, int nrhs, const double *b, double *x, double *r);
 
 /* Write / read the stored eigenpairs to / from a binary file (header with
  * lattice, count, precision and checksum).  Loading recomputes the eigenvalues

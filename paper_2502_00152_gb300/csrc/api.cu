@@ -10,6 +10,7 @@
 using namespace hisq;
 
 namespace hisq {
+void tc_forget(hisq_ctx *ctx);
 
 int log_level()
 {
@@ -135,6 +136,7 @@ void hisq_default_solve_params(hisq_solve_params *p)
     p->n_defl = 0;
     p->delta_tr = 1e-3;
     p->compute_full_residual = 1;
+    p->batch = 1;
 }
 
 void hisq_default_eig_params(hisq_eig_params *p)
@@ -205,6 +207,14 @@ hisq_status hisq_create(const int dims[4], int t_antiperiodic, int device, void 
     if (cudaHostAlloc((void **)&ctx->monitor_h, sizeof(double) * ctx->monitor_len, cudaHostAllocMapped) != cudaSuccess)
         return fail(HISQ_ERR_OOM);
     if (cudaHostGetDevicePointer((void **)&ctx->monitor_d, ctx->monitor_h, 0) != cudaSuccess) return fail(HISQ_ERR_CUDA);
+    ctx->bscal = (BatchScalars *)dev_alloc(ctx, sizeof(BatchScalars));
+    ctx->bpartials = (double *)dev_alloc(ctx, sizeof(double) * ctx->max_red_blocks * kMaxBatch);
+    if (!ctx->bscal || !ctx->bpartials) return fail(HISQ_ERR_OOM);
+    if (cudaMemset(ctx->bscal, 0, sizeof(BatchScalars)) != cudaSuccess) return fail(HISQ_ERR_CUDA);
+    if (cudaHostAlloc((void **)&ctx->bmonitor_h, sizeof(double) * ctx->bmonitor_len * kMaxBatch,
+                      cudaHostAllocMapped) != cudaSuccess)
+        return fail(HISQ_ERR_OOM);
+    if (cudaHostGetDevicePointer((void **)&ctx->bmonitor_d, ctx->bmonitor_h, 0) != cudaSuccess) return fail(HISQ_ERR_CUDA);
     *out = ctx;
     return HISQ_OK;
 }
@@ -214,10 +224,13 @@ void hisq_destroy(hisq_ctx *ctx)
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    tc_forget(ctx);
     for (int p = 0; p < 2; p++) {
         cudaFree(ctx->links_d[p]);
         cudaFree(ctx->links_f[p]);
         cudaFree(ctx->links_f12[p]);
+        cudaFree(ctx->links_h[p]);
+        cudaFree(ctx->links_h12[p]);
     }
     for (int i = 0; i < BUF_COUNT; i++) cudaFree(ctx->bufs[i]);
     cudaFree(ctx->eig.vecs);
@@ -225,6 +238,9 @@ void hisq_destroy(hisq_ctx *ctx)
     cudaFree(ctx->ticket);
     cudaFree(ctx->scal);
     if (ctx->monitor_h) cudaFreeHost(ctx->monitor_h);
+    cudaFree(ctx->bscal);
+    cudaFree(ctx->bpartials);
+    if (ctx->bmonitor_h) cudaFreeHost(ctx->bmonitor_h);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -247,13 +263,23 @@ hisq_status hisq_load_links(hisq_ctx *ctx, const double *fat, const double *lng,
         ctx->links_f[p] = nullptr;
         dev_free(ctx, ctx->links_f12[p], size_t(Vh) * 4 * 6 * 16);
         ctx->links_f12[p] = nullptr;
+        dev_free(ctx, ctx->links_h[p], size_t(Vh) * (ctx->long_recon == 12 ? 4 : 8) * 9 * 8);
+        ctx->links_h[p] = nullptr;
+        dev_free(ctx, ctx->links_h12[p], size_t(Vh) * 4 * 6 * 8);
+        ctx->links_h12[p] = nullptr;
     }
     ctx->links_loaded = false;
     for (int p = 0; p < 2; p++) {
         ctx->links_d[p] = (double2 *)dev_alloc(ctx, size_t(Vh) * 16 * 9 * 16);
         ctx->links_f[p] = (float4 *)dev_alloc(ctx, size_t(Vh) * (long_recon == 12 ? 4 : 8) * 9 * 16);
-        if (long_recon == 12) ctx->links_f12[p] = (float4 *)dev_alloc(ctx, size_t(Vh) * 4 * 6 * 16);
-        if (!ctx->links_d[p] || !ctx->links_f[p] || (long_recon == 12 && !ctx->links_f12[p])) return HISQ_ERR_OOM;
+        ctx->links_h[p] = (uint2 *)dev_alloc(ctx, size_t(Vh) * (long_recon == 12 ? 4 : 8) * 9 * 8);
+        if (long_recon == 12) {
+            ctx->links_f12[p] = (float4 *)dev_alloc(ctx, size_t(Vh) * 4 * 6 * 16);
+            ctx->links_h12[p] = (uint2 *)dev_alloc(ctx, size_t(Vh) * 4 * 6 * 8);
+        }
+        if (!ctx->links_d[p] || !ctx->links_f[p] || !ctx->links_h[p] ||
+            (long_recon == 12 && (!ctx->links_f12[p] || !ctx->links_h12[p])))
+            return HISQ_ERR_OOM;
     }
     ctx->long_recon = long_recon;
     ctx->long_scale = long_recon == 12 ? long_scale : 1.0;
@@ -305,12 +331,20 @@ static hisq_status download_full(hisq_ctx *ctx, const double *dev, double *host)
         if (s_ != HISQ_OK) return s_;           \
     } while (0)
 
-hisq_status hisq_apply_dslash(hisq_ctx *ctx, int out_parity, int precision, const double *in, double *out)
+static bool bad_precisions(int prec, int link_prec)
+{
+    if (prec != 64 && prec != 32 && prec != 16) return true;
+    if (link_prec != 64 && link_prec != 32 && link_prec != 16) return true;
+    return (prec == 64) != (link_prec == 64);
+}
+
+hisq_status hisq_apply_dslash(hisq_ctx *ctx, int out_parity, int precision, int link_precision, const double *in,
+                              double *out)
 {
     if (!ctx) return HISQ_ERR_INVALID_ARG;
     if (!in || !out || (out_parity != 0 && out_parity != 1)) return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad argument");
-    if (precision != 64 && precision != 32 && precision != 16)
-        return set_err(ctx, HISQ_ERR_INVALID_ARG, "precision must be 64, 32 or 16");
+    if (bad_precisions(precision, link_precision))
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "precisions must be 64/64 or 32|16 with 32|16 links");
     if (!ctx->links_loaded) return set_err(ctx, HISQ_ERR_STATE, "links not loaded");
     HISQ_CUDA(cudaSetDevice(ctx->device));
     const int Vh = ctx->g.Vh;
@@ -320,18 +354,18 @@ hisq_status hisq_apply_dslash(hisq_ctx *ctx, int out_parity, int precision, cons
     void *b = get_buf(ctx, BUF_TEST_C, spinor_bytes(precision, Vh));
     if (!a || !b) return HISQ_ERR_OOM;
     TRY(launch_gather_parity(ctx, full, 1 - out_parity, precision, a));
-    TRY(launch_dslash(ctx, out_parity, precision, precision == 64 ? 64 : 32, a, b, 0, nullptr, 0, nullptr, 1.0, -1));
+    TRY(launch_dslash(ctx, out_parity, precision, link_precision, a, b, 0, nullptr, 0, nullptr, 1.0, -1));
     HISQ_CUDA(cudaMemsetAsync(full, 0, size_t(ctx->g.V) * 48, ctx->stream));
     TRY(launch_scatter_parity(ctx, b, precision, out_parity, full));
     return download_full(ctx, full, out);
 }
 
-hisq_status hisq_apply_normal_op(hisq_ctx *ctx, int precision, const double *in, double *out)
+hisq_status hisq_apply_normal_op(hisq_ctx *ctx, int precision, int link_precision, const double *in, double *out)
 {
     if (!ctx) return HISQ_ERR_INVALID_ARG;
     if (!in || !out) return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad argument");
-    if (precision != 64 && precision != 32 && precision != 16)
-        return set_err(ctx, HISQ_ERR_INVALID_ARG, "precision must be 64, 32 or 16");
+    if (bad_precisions(precision, link_precision))
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "precisions must be 64/64 or 32|16 with 32|16 links");
     if (!ctx->links_loaded) return set_err(ctx, HISQ_ERR_STATE, "links not loaded");
     if (!(ctx->mass > 0)) return set_err(ctx, HISQ_ERR_STATE, "mass not set");
     HISQ_CUDA(cudaSetDevice(ctx->device));
@@ -342,7 +376,7 @@ hisq_status hisq_apply_normal_op(hisq_ctx *ctx, int precision, const double *in,
     void *b = get_buf(ctx, BUF_TEST_C, spinor_bytes(precision, Vh));
     void *t = get_buf(ctx, BUF_TMP, spinor_bytes(precision, Vh));
     if (!a || !b || !t) return HISQ_ERR_OOM;
-    const int lp = precision == 64 ? 64 : 32;
+    const int lp = link_precision;
     const double m4 = 4.0 * ctx->mass * ctx->mass;
     TRY(launch_gather_parity(ctx, full, 0, precision, a));
     TRY(launch_dslash(ctx, 1, precision, lp, a, t, 0, nullptr, 0, nullptr, 1.0, -1));       // t = D_oe a

@@ -1,0 +1,345 @@
+// batch_solver.cu -- several right-hand sides solved together (the paper's
+// outlook, Section 4: batched solves raise the arithmetic intensity).
+//
+// Each right-hand side keeps its own CG recurrence, reliable updates (Section 3,
+// delta_rd) and re-deflations (delta_tr); the sloppy operator is applied to all
+// active right-hand sides in one batched launch, which reads every link once
+// per iteration instead of once per right-hand side.  A right-hand side leaves
+// the active set (its slot is removed from the launch list) as soon as its FP64
+// true residual meets the tolerance.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace hisq {
+
+double *eig_eps_dev(hisq_ctx *ctx);
+hisq_status read_slots(hisq_ctx *ctx, int slot0, int n, double *out);
+hisq_status deflate_add(hisq_ctx *ctx, int n, const double *r, double *x);
+hisq_status launch_defl_expand2(hisq_ctx *ctx, int n, int vprec, const void *V, const double *c_dev,
+                                const double *eps_dev, double shift, double *x, double *r);
+hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, const double *rnorm);
+
+// the tensor-core batched deflation applies to FP32-stored eigenvectors, up to
+// 512 of them and 32 right-hand sides per call
+static bool tc_eligible(const hisq_ctx *ctx, int n, int k)
+{
+    return ctx->eig.prec == 32 && n >= 1 && n <= 512 && k >= 2;
+}
+
+#define TRY(x)                                  \
+    do {                                        \
+        hisq_status s_ = (x);                   \
+        if (s_ != HISQ_OK) return s_;           \
+    } while (0)
+
+enum { BS_Y = 0, BS_ETAE = 1, BS_ETAO = 2, BS_R = 3, BS_RE = 4, BS_RO = 5, BS_PP = 6 };
+
+static hisq_status residual_hi_b(hisq_ctx *ctx, const double *b, const double *x, double *r, double *tmp_odd, int slot)
+{
+    const double m4 = 4.0 * ctx->mass * ctx->mass;
+    TRY(launch_dslash(ctx, 1, 64, 64, x, tmp_odd, 0, nullptr, 0, nullptr, 1.0, -1));
+    return launch_dslash(ctx, 0, 64, 64, tmp_odd, r, -m4, x, 1.0, b, 1.0, slot);
+}
+
+static hisq_status deflate_pair_b(hisq_ctx *ctx, int n, const double *b, double *r, double *x, double *t_odd, int slot)
+{
+    if (n > 4096 || ctx->eig.prec != 32) { // see deflate_pair in solver.cu
+        TRY(deflate_add(ctx, n, r, x));
+        return residual_hi_b(ctx, b, x, r, t_odd, slot);
+    }
+    double *eps = eig_eps_dev(ctx);
+    double *c = (double *)get_buf(ctx, BUF_DEFL_C, sizeof(double) * 2 * (n > 0 ? n : 1));
+    if (!eps || !c) return set_err(ctx, HISQ_ERR_OOM, "deflation buffers");
+    TRY(launch_defl_project(ctx, n, ctx->eig.prec, ctx->eig.vecs, 64, r, c));
+    TRY(launch_defl_expand2(ctx, n, ctx->eig.prec, ctx->eig.vecs, c, eps, 4.0 * ctx->mass * ctx->mass, x, r));
+    return launch_norm2(ctx, 64, r, slot);
+}
+
+// copy selected fields of the batch scalars of right-hand side j to the device
+static hisq_status set_rhs_scalars(hisq_ctx *ctx, int j, double rr, double pp)
+{
+    HISQ_CUDA(cudaMemcpyAsync(&ctx->bscal->rr[j], &rr, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    HISQ_CUDA(cudaMemcpyAsync(&ctx->bscal->pp[j], &pp, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    return HISQ_OK;
+}
+
+static hisq_status set_active(hisq_ctx *ctx, const std::vector<int> &act)
+{
+    int buf[kMaxBatch + 1];
+    buf[0] = int(act.size());
+    for (size_t q = 0; q < act.size(); q++) buf[1 + q] = act[q];
+    HISQ_CUDA(cudaMemcpyAsync(&ctx->bscal->kact, buf, sizeof(int) * (1 + act.size()), cudaMemcpyHostToDevice,
+                              ctx->stream));
+    HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    return HISQ_OK;
+}
+
+// Solve M psi_j = eta_j for k <= kMaxBatch right-hand sides together; eta, psi:
+// k FP64 full-lattice device fields (stride V*48 bytes).
+hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const double *eta, double *psi, int k,
+                          hisq_solve_stats *stats)
+{
+    static_assert(offsetof(BatchScalars, idx) == offsetof(BatchScalars, kact) + sizeof(int), "kact, idx adjacent");
+    const int Vh = ctx->g.Vh;
+    const size_t full = size_t(ctx->g.V) * 6;
+    const double m = ctx->mass, m4 = 4.0 * m * m;
+    const int prec = P->precision_sloppy, lprec = P->link_precision_sloppy, xprec = 32;
+    if (k < 1 || k > kMaxBatch) return set_err(ctx, HISQ_ERR_INVALID_ARG, "batch of 1..%d right-hand sides", kMaxBatch);
+    if (prec != 32 && prec != 16) return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched solve: sloppy precision 32 or 16");
+    if (lprec != 32) return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched solve: FP32 sloppy links");
+    const size_t s64 = spinor_bytes(64, Vh), ssl = spinor_bytes(prec, Vh), sx = spinor_bytes(xprec, Vh);
+    char *Y = (char *)get_buf(ctx, BUF_B_Y, s64 * k);
+    char *XH = (char *)get_buf(ctx, BUF_B_XHI, s64 * k);
+    char *RH = (char *)get_buf(ctx, BUF_B_RHI, s64 * k);
+    char *XS = (char *)get_buf(ctx, BUF_B_XSL, sx * k);
+    char *RS = (char *)get_buf(ctx, BUF_B_RSL, ssl * k);
+    char *PP = (char *)get_buf(ctx, BUF_B_P, ssl * k);
+    char *TT = (char *)get_buf(ctx, BUF_B_TMP, ssl * k);
+    double *eta_e = (double *)get_buf(ctx, BUF_ETA_E, s64);
+    double *eta_o = (double *)get_buf(ctx, BUF_ETA_O, s64);
+    double *t_hi = (double *)get_buf(ctx, BUF_TMPHI, s64);
+    double *psi_o = (double *)get_buf(ctx, BUF_PSI_O, s64);
+    if (!Y || !XH || !RH || !XS || !RS || !PP || !TT || !eta_e || !eta_o || !t_hi || !psi_o) return HISQ_ERR_OOM;
+    auto y = [&](int j) { return (double *)(Y + s64 * j); };
+    auto xh = [&](int j) { return (double *)(XH + s64 * j); };
+    auto rh = [&](int j) { return (double *)(RH + s64 * j); };
+    auto xs = [&](int j) { return (void *)(XS + sx * j); };
+    auto rs = [&](int j) { return (void *)(RS + ssl * j); };
+    auto pj = [&](int j) { return (void *)(PP + ssl * j); };
+
+    int n_defl = 0;
+    if (P->deflate) {
+        if (ctx->eig.n <= 0) return set_err(ctx, HISQ_ERR_STATE, "deflation requested but no eigenpairs stored");
+        n_defl = P->n_defl > 0 ? std::min(P->n_defl, ctx->eig.n) : ctx->eig.n;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<double> target(k), etanorm(k), ynorm(k), rt(k), r_last(k), r_defl(k), r_best(k), rn_seen(k);
+    std::vector<int> noprog(k, 0), done(k, 0), its(k, 0), last_upd(k, 0);
+    std::vector<hisq_solve_stats> st(k);
+    for (int j = 0; j < k; j++) {
+        memset(&st[j], 0, sizeof st[j]);
+        st[j].full_residual = -1;
+    }
+    double defl_s = 0;
+
+    // (a2) sources, (a8) deflated guesses
+    for (int j = 0; j < k; j++) {
+        const double *e = eta + full * j;
+        TRY(launch_gather_parity(ctx, e, 0, 64, eta_e));
+        TRY(launch_gather_parity(ctx, e, 1, 64, eta_o));
+        TRY(launch_norm2(ctx, 64, eta_e, BS_ETAE));
+        TRY(launch_norm2(ctx, 64, eta_o, BS_ETAO));
+        TRY(launch_dslash(ctx, 0, 64, 64, eta_o, y(j), 2.0 * m, eta_e, 0, nullptr, -1.0, BS_Y));
+        double nrm[3];
+        TRY(read_slots(ctx, BS_Y, 3, nrm));
+        ynorm[j] = std::sqrt(nrm[0]);
+        etanorm[j] = std::sqrt(nrm[1] + nrm[2]);
+        if (!std::isfinite(ynorm[j]) || !std::isfinite(etanorm[j]))
+            return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite source %d", j);
+        target[j] = P->tol * std::fmin(ynorm[j], 2.0 * m * etanorm[j]);
+        HISQ_CUDA(cudaMemsetAsync(xh(j), 0, s64, ctx->stream));
+        HISQ_CUDA(cudaMemcpyAsync(rh(j), y(j), s64, cudaMemcpyDeviceToDevice, ctx->stream));
+        rt[j] = ynorm[j];
+    }
+    // deflated guesses of all right-hand sides: one tensor-core projection and
+    // one expansion for the whole batch, else one pair of passes per RHS
+    if (n_defl > 0) {
+        auto d0 = std::chrono::steady_clock::now();
+        if (tc_eligible(ctx, n_defl, k)) {
+            for (int j0 = 0; j0 < k; j0 += 32) {
+                const int kb = std::min(32, k - j0);
+                TRY(tc_deflate_batch(ctx, n_defl, kb, rh(j0), xh(j0), &ynorm[j0]));
+            }
+            for (int j = 0; j < k; j++) {
+                double r2;
+                TRY(launch_norm2(ctx, 64, rh(j), BS_R));
+                TRY(read_slots(ctx, BS_R, 1, &r2));
+                rt[j] = std::sqrt(r2);
+            }
+        } else {
+            for (int j = 0; j < k; j++) {
+                double r2;
+                TRY(deflate_pair_b(ctx, n_defl, y(j), rh(j), xh(j), t_hi, BS_R));
+                TRY(read_slots(ctx, BS_R, 1, &r2));
+                rt[j] = std::sqrt(r2);
+            }
+        }
+        defl_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - d0).count();
+    }
+    for (int j = 0; j < k; j++) {
+        r_last[j] = r_defl[j] = r_best[j] = rn_seen[j] = rt[j];
+        if (etanorm[j] == 0 || rt[j] <= target[j]) {
+            done[j] = 1;
+            st[j].converged = 1;
+            continue;
+        }
+        TRY(launch_convert(ctx, rh(j), 64, rs(j), prec));
+        TRY(launch_convert(ctx, rh(j), 64, pj(j), prec));
+        TRY(launch_zero(ctx, xs(j), xprec));
+        TRY(set_rhs_scalars(ctx, j, rt[j] * rt[j], rt[j] * rt[j]));
+    }
+    std::vector<int> act;
+    for (int j = 0; j < k; j++)
+        if (!done[j]) act.push_back(j);
+    {
+        double hm4 = m4;
+        long long it0 = 0;
+        HISQ_CUDA(cudaMemcpyAsync(&ctx->bscal->m4, &hm4, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        HISQ_CUDA(cudaMemcpyAsync(&ctx->bscal->iter, &it0, sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+    }
+    TRY(set_active(ctx, act));
+
+    cudaEvent_t ev[2];
+    HISQ_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    HISQ_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    struct EvFree {
+        cudaEvent_t *e;
+        ~EvFree()
+        {
+            cudaEventDestroy(e[0]);
+            cudaEventDestroy(e[1]);
+        }
+    } evfree{ev};
+    const long long maxit = P->max_iter > 0 ? P->max_iter : 1;
+    long long it = 0, checked = 0;
+    std::vector<std::vector<int>> act_at(2); // active list of the iteration in each event slot
+    while (!act.empty()) {
+        const bool force = it >= maxit;
+        if (!force) {
+            const int ka = int(act.size());
+            TRY(launch_mrhs_dslash_tt(ctx, prec, lprec, PP, TT, ka));
+            TRY(launch_mrhs_dslash_update(ctx, prec, lprec, TT, PP, XS, RS, ka));
+            TRY(launch_mrhs_p_update(ctx, prec, RS, PP, ka));
+            HISQ_CUDA(cudaEventRecord(ev[it & 1], ctx->stream));
+            act_at[it & 1] = act;
+            for (int j : act) its[j]++;
+            it++;
+        }
+        std::vector<int> upd;
+        const long long jj = it - 2;
+        if (force) {
+            upd = act;
+        } else if (jj >= checked) {
+            HISQ_CUDA(cudaEventSynchronize(ev[jj & 1]));
+            for (int j : act_at[jj & 1]) {
+                const double rr = ctx->bmonitor_h[size_t(jj % ctx->bmonitor_len) * kMaxBatch + j];
+                if (!std::isfinite(rr)) {
+                    cudaStreamSynchronize(ctx->stream);
+                    return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite residual of right-hand side %d", j);
+                }
+                const double rn = std::sqrt(rr);
+                rn_seen[j] = rn;
+                if (rn < target[j] || rn < P->delta_rd * r_last[j] || rn > 1e3 * r_last[j] ||
+                    its[j] - last_upd[j] >= 1000)
+                    upd.push_back(j);
+            }
+            checked = jj + 1;
+        }
+        if (upd.empty()) continue;
+        HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+        checked = it;
+        bool changed = false;
+        for (int j : upd) {
+            // reliable update of right-hand side j (FP64 true residual)
+            TRY(launch_axpy_d(ctx, 1.0, xs(j), xprec, xh(j)));
+            TRY(residual_hi_b(ctx, y(j), xh(j), rh(j), t_hi, BS_R));
+            double r2;
+            TRY(read_slots(ctx, BS_R, 1, &r2));
+            if (!std::isfinite(r2)) return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite true residual");
+            rt[j] = std::sqrt(r2);
+            st[j].reliable_updates++;
+            last_upd[j] = its[j];
+            bool finish = false;
+            if (rt[j] <= target[j]) {
+                st[j].converged = 1;
+                finish = true;
+            } else if (force || its[j] >= maxit) {
+                finish = true;
+            } else if (rt[j] < 0.5 * r_best[j]) {
+                r_best[j] = rt[j];
+                noprog[j] = 0;
+            } else if (++noprog[j] >= 8) {
+                set_err(ctx, HISQ_ERR_NOT_CONVERGED, "stagnation of right-hand side %d", j);
+                finish = true;
+            }
+            if (finish) {
+                done[j] = 1;
+                changed = true;
+                continue;
+            }
+            bool restart = rt[j] > 10.0 * rn_seen[j];
+            if (n_defl > 0 && P->delta_tr > 0 && rt[j] < P->delta_tr * r_defl[j]) {
+                auto d0 = std::chrono::steady_clock::now();
+                TRY(deflate_pair_b(ctx, n_defl, y(j), rh(j), xh(j), t_hi, BS_R));
+                TRY(read_slots(ctx, BS_R, 1, &r2));
+                defl_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - d0).count();
+                rt[j] = std::sqrt(r2);
+                r_defl[j] = rt[j];
+                st[j].redeflations++;
+                restart = true;
+                if (rt[j] <= target[j]) {
+                    st[j].converged = 1;
+                    done[j] = 1;
+                    changed = true;
+                    continue;
+                }
+            }
+            TRY(launch_convert(ctx, rh(j), 64, rs(j), prec));
+            TRY(launch_zero(ctx, xs(j), xprec));
+            double pp = rt[j] * rt[j];
+            if (restart) {
+                TRY(launch_convert(ctx, rh(j), 64, pj(j), prec));
+            } else {
+                TRY(launch_norm2(ctx, prec, pj(j), BS_PP));
+                TRY(read_slots(ctx, BS_PP, 1, &pp));
+            }
+            TRY(set_rhs_scalars(ctx, j, rt[j] * rt[j], pp));
+            r_last[j] = rt[j];
+        }
+        if (changed) {
+            act.clear();
+            for (int j = 0; j < k; j++)
+                if (!done[j]) act.push_back(j);
+        }
+        TRY(set_active(ctx, act));
+    }
+    HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+
+    // (a9) reconstruction and FP64 full residuals
+    hisq_status worst = HISQ_OK;
+    for (int j = 0; j < k; j++) {
+        const double *e = eta + full * j;
+        double *out = psi + full * j;
+        TRY(launch_gather_parity(ctx, e, 0, 64, eta_e));
+        TRY(launch_gather_parity(ctx, e, 1, 64, eta_o));
+        TRY(launch_dslash(ctx, 1, 64, 64, xh(j), psi_o, 1.0 / (2.0 * m), eta_o, 0, nullptr, -1.0 / (2.0 * m), -1));
+        if (P->compute_full_residual && etanorm[j] > 0) {
+            TRY(launch_dslash(ctx, 0, 64, 64, psi_o, rh(j), -2.0 * m, xh(j), 1.0, eta_e, -1.0, BS_RE));
+            TRY(launch_dslash(ctx, 1, 64, 64, xh(j), t_hi, -2.0 * m, psi_o, 1.0, eta_o, -1.0, BS_RO));
+            double rr[2];
+            TRY(read_slots(ctx, BS_RE, 2, rr));
+            st[j].full_residual = std::sqrt(rr[0] + rr[1]) / etanorm[j];
+        } else if (etanorm[j] == 0) {
+            st[j].full_residual = 0;
+        }
+        TRY(launch_scatter_parity(ctx, xh(j), 64, 0, out));
+        TRY(launch_scatter_parity(ctx, psi_o, 64, 1, out));
+        st[j].iterations = its[j];
+        st[j].even_residual = ynorm[j] > 0 ? rt[j] / ynorm[j] : 0;
+        if (!st[j].converged) worst = HISQ_ERR_NOT_CONVERGED;
+    }
+    HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int j = 0; j < k; j++) {
+        st[j].seconds_total = secs / k;
+        st[j].seconds_deflate = defl_s / k;
+        if (stats) stats[j] = st[j];
+    }
+    return worst;
+}
+
+} // namespace hisq

@@ -281,7 +281,7 @@ constexpr int kDeflSites = 4096;  // sites per block in the projection
 
 // partial[i][chunk] = sum over the chunk's sites of v_i^dag b
 template <class SV, class SB>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     k_defl_project(int Vh, int n, const char *__restrict__ V0, size_t vstride, SB b, double2 *part, int nchunks)
 {
     const int g0 = blockIdx.x * kDeflVG;
@@ -606,6 +606,82 @@ hisq_status launch_defl_project_ext(hisq_ctx *ctx, int n, int vprec, const void 
     ctx->launches += 2;
     k_defl_finish<<<(n + 127) / 128, 128, 0, ctx->stream>>>(n, nchunks, part, (double2 *)c_dev, nullptr, 0.0);
     LAUNCH_CHECK("defl_finish_ext");
+    return HISQ_OK;
+}
+
+} // namespace hisq
+
+namespace hisq {
+
+// One pass over the eigenvectors for a deflation step on an FP64 pair (x, r):
+//   x += sum_i c_i / (eps_i + shift) v_i,   r -= sum_i c_i v_i
+// With A v_i = lambda_i v_i (lambda_i = eps_i + shift) the second update is the
+// residual change of the first, so r stays b - A x without applying A.
+template <class SV>
+__global__ void __launch_bounds__(256) k_defl_expand2(int Vh, int n, const char *__restrict__ V0, size_t vstride,
+                                                      const double2 *c, const double *eps, double shift, SpinorD x,
+                                                      SpinorD r)
+{
+    extern __shared__ float smem[];
+    float2 *sc = reinterpret_cast<float2 *>(smem);
+    float *sinv = smem + 2 * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        sc[i] = make_float2(float(c[i].x), float(c[i].y));
+        sinv[i] = float(1.0 / (eps[i] + shift));
+    }
+    __syncthreads();
+    for (int cb = blockIdx.x * blockDim.x + threadIdx.x; cb < Vh; cb += gridDim.x * blockDim.x) {
+        CVec<float> ax, ar;
+        ax.zero();
+        ar.zero();
+#pragma unroll 4
+        for (int i = 0; i < n; i++) {
+            CVec<float> v = spinor_at<SV>(V0, vstride, i, Vh).load(cb);
+            const float2 w = sc[i];
+            const float s = sinv[i];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float pr = fmaf(w.x, v.re[k], -w.y * v.im[k]);
+                const float pi = fmaf(w.x, v.im[k], w.y * v.re[k]);
+                ar.re[k] += pr;
+                ar.im[k] += pi;
+                ax.re[k] = fmaf(s, pr, ax.re[k]);
+                ax.im[k] = fmaf(s, pi, ax.im[k]);
+            }
+        }
+        CVec<double> xv = x.load(cb), rv = r.load(cb);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            xv.re[k] += double(ax.re[k]);
+            xv.im[k] += double(ax.im[k]);
+            rv.re[k] -= double(ar.re[k]);
+            rv.im[k] -= double(ar.im[k]);
+        }
+        x.store(cb, xv);
+        r.store(cb, rv);
+    }
+}
+
+hisq_status launch_defl_expand2(hisq_ctx *ctx, int n, int vprec, const void *V, const double *c_dev,
+                                const double *eps_dev, double shift, double *x, double *r)
+{
+    const int Vh = ctx->g.Vh;
+    if (n > 4096) return set_err(ctx, HISQ_ERR_INVALID_ARG, "dual expansion supports at most 4096 vectors");
+    const size_t smem = size_t(n) * 12;
+    const size_t stride = spinor_bytes(vprec, Vh);
+    SpinorD xs = make_spinorD(x, Vh), rs = make_spinorD(r, Vh);
+    if (vprec == 32) {
+        auto k = k_defl_expand2<SpinorF>;
+        int grid = grid_for(ctx, Vh, 256, occ(k, 256, smem));
+        k<<<grid, 256, smem, ctx->stream>>>(Vh, n, (const char *)V, stride, (const double2 *)c_dev, eps_dev, shift, xs, rs);
+    } else if (vprec == 16) {
+        auto k = k_defl_expand2<SpinorH>;
+        int grid = grid_for(ctx, Vh, 256, occ(k, 256, smem));
+        k<<<grid, 256, smem, ctx->stream>>>(Vh, n, (const char *)V, stride, (const double2 *)c_dev, eps_dev, shift, xs, rs);
+    } else {
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "eigenvector precision must be 32 or 16");
+    }
+    LAUNCH_CHECK("defl_expand2");
     return HISQ_OK;
 }
 

@@ -79,10 +79,79 @@ struct EpiCG {
     }
 };
 
+// ------------------------------------------------------------- link formats
+// FP32, kinds per mu = 2 (fat + long, 18 reals) or 1 (fat only; long in recon 12)
+struct LinksFv {
+    const float4 *base;
+    int Vh;
+    int nk;
+    typedef float real;
+    __device__ __forceinline__ void load(int mu, int kind, int i, CMat<float> &f, CMat<float> &b) const
+    {
+        const float4 *q = base + size_t((mu * nk + kind) * 9) * Vh + i;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            float4 a = __ldcs(q + size_t(k) * Vh);
+            f.re[k] = a.x;
+            f.im[k] = a.y;
+            b.re[k] = a.z;
+            b.im[k] = a.w;
+        }
+    }
+};
+
+__device__ __forceinline__ float2 h2f(unsigned u)
+{
+    __half2 h = *reinterpret_cast<__half2 *>(&u);
+    return __half22float2(h);
+}
+
+// FP16: uint2 = (fwd_k, bwd_k) as two half2, [mu][kind][k<9][Vh]
+struct LinksHv {
+    const uint2 *base;
+    int Vh;
+    int nk;
+    typedef float real;
+    __device__ __forceinline__ void load(int mu, int kind, int i, CMat<float> &f, CMat<float> &b) const
+    {
+        const uint2 *q = base + size_t((mu * nk + kind) * 9) * Vh + i;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            uint2 a = __ldcs(q + size_t(k) * Vh);
+            float2 x = h2f(a.x), y = h2f(a.y);
+            f.re[k] = x.x;
+            f.im[k] = x.y;
+            b.re[k] = y.x;
+            b.im[k] = y.y;
+        }
+    }
+};
+
+// FP16 12-real long links: uint2 (fwd_k, bwd_k), rows 0,1 of the SU(3) factor
+struct LinksH12 {
+    const uint2 *base;
+    int Vh;
+    __device__ __forceinline__ void load(int mu, int i, CMat<float> &f, CMat<float> &b) const
+    {
+        const uint2 *q = base + size_t(mu * 6) * Vh + i;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            uint2 a = __ldcs(q + size_t(k) * Vh);
+            float2 x = h2f(a.x), y = h2f(a.y);
+            f.re[k] = x.x;
+            f.im[k] = x.y;
+            b.re[k] = y.x;
+            b.im[k] = y.y;
+        }
+        su3_third_row(f);
+        su3_third_row(b);
+    }
+};
+
 // ------------------------------------------------------------- the kernel
-template <class SIn, class Lk, bool R12, class Epi>
+template <class SIn, class Lk, class L12T, bool R12, class Epi>
 __global__ void __launch_bounds__(256)
-    k_dslash(Geom g, int par, Lk L, LinksF12 L12, float c3, SIn in, Epi epi, RedArgs ra, int do_red)
+    k_dslash(Geom g, int par, Lk L, L12T L12, float c3, SIn in, Epi epi, RedArgs ra, int do_red)
 {
     typedef typename Lk::real R;
     double red = 0;
@@ -140,89 +209,71 @@ static int blocks_per_sm(K kernel)
     return n;
 }
 
-template <class SIn, class Lk, bool R12, class Epi>
-static hisq_status run_dslash(hisq_ctx *ctx, int par, const Lk &L, const SIn &in, const Epi &epi,
+template <class SIn, class Lk, class L12T, bool R12, class Epi>
+static hisq_status run_dslash(hisq_ctx *ctx, int par, const Lk &L, const L12T &L12, const SIn &in, const Epi &epi,
                               RedArgs ra, int do_red)
 {
-    auto kern = k_dslash<SIn, Lk, R12, Epi>;
+    auto kern = k_dslash<SIn, Lk, L12T, R12, Epi>;
     static int bps = -1;
     if (bps < 0) bps = blocks_per_sm(kern);
     const int grid = grid_for(ctx, ctx->g.Vh, 256, bps);
-    LinksF12 l12{nullptr, ctx->g.Vh};
-    if (R12) l12.base = ctx->links_f12[par];
-    kern<<<grid, 256, 0, ctx->stream>>>(ctx->g, par, L, l12, float(ctx->long_scale), in, epi, ra, do_red);
+    kern<<<grid, 256, 0, ctx->stream>>>(ctx->g, par, L, L12, float(ctx->long_scale), in, epi, ra, do_red);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_err(ctx, e, "dslash launch");
     return HISQ_OK;
 }
 
-static LinksD links_d(hisq_ctx *ctx, int par) { return LinksD{ctx->links_d[par], ctx->g.Vh}; }
-
-struct LinksFv { // FP32 links, kinds per mu = 2 (recon 18) or 1 (fat only, recon 12)
-    const float4 *base;
-    int Vh;
-    int nk;
-    typedef float real;
-    __device__ __forceinline__ void load(int mu, int kind, int i, CMat<float> &f, CMat<float> &b) const
-    {
-        const float4 *q = base + size_t((mu * nk + kind) * 9) * Vh + i;
-#pragma unroll
-        for (int k = 0; k < 9; k++) {
-            float4 a = __ldcs(q + size_t(k) * Vh);
-            f.re[k] = a.x;
-            f.im[k] = a.y;
-            b.re[k] = a.z;
-            b.im[k] = a.w;
-        }
-    }
-};
-
-static LinksFv links_f(hisq_ctx *ctx, int par)
-{
-    return LinksFv{ctx->links_f[par], ctx->g.Vh, ctx->long_recon == 12 ? 1 : 2};
-}
-
-template <class S>
-static hisq_status dslash_prec(hisq_ctx *ctx, int par, int link_prec, S in, S out, double a, const void *x,
-                               double b, const void *y, double c, int norm_slot, S sx, S sy)
+// Run the Dslash with output parity `par` on links of precision link_prec
+// (64, 32 or 16) in the context's long-link format.
+template <class S, class Epi>
+static hisq_status run_any(hisq_ctx *ctx, int par, int link_prec, const S &in, const Epi &epi, RedArgs ra, int dored)
 {
     typedef typename S::real R;
-    EpiXpay<S> epi{out, sx, sy, R(a), R(b), R(c), x != nullptr, y != nullptr, norm_slot >= 0};
-    RedArgs ra = red_args(ctx, FIN_STORE, norm_slot < 0 ? 0 : norm_slot);
-    const int dored = norm_slot >= 0;
-    const int inpar = par; // output parity; links indexed by output parity
+    const int Vh = ctx->g.Vh;
+    const bool r12 = ctx->long_recon == 12;
+    const int nk = r12 ? 1 : 2;
     if (link_prec == 64) {
-        if constexpr (sizeof(R) == 8) return run_dslash<S, LinksD, false>(ctx, inpar, links_d(ctx, par), in, epi, ra, dored);
+        if constexpr (sizeof(R) == 8)
+            return run_dslash<S, LinksD, LinksF12, false>(ctx, par, LinksD{ctx->links_d[par], Vh}, LinksF12{nullptr, Vh},
+                                                          in, epi, ra, dored);
         return set_err(ctx, HISQ_ERR_INVALID_ARG, "FP64 links need FP64 vectors");
     }
     if constexpr (sizeof(R) == 4) {
-        if (ctx->long_recon == 12)
-            return run_dslash<S, LinksFv, true>(ctx, inpar, links_f(ctx, par), in, epi, ra, dored);
-        return run_dslash<S, LinksFv, false>(ctx, inpar, links_f(ctx, par), in, epi, ra, dored);
+        if (link_prec == 32) {
+            LinksFv L{ctx->links_f[par], Vh, nk};
+            if (r12) return run_dslash<S, LinksFv, LinksF12, true>(ctx, par, L, LinksF12{ctx->links_f12[par], Vh}, in, epi, ra, dored);
+            return run_dslash<S, LinksFv, LinksF12, false>(ctx, par, L, LinksF12{nullptr, Vh}, in, epi, ra, dored);
+        }
+        if (link_prec == 16) {
+            LinksHv L{ctx->links_h[par], Vh, nk};
+            if (r12) return run_dslash<S, LinksHv, LinksH12, true>(ctx, par, L, LinksH12{ctx->links_h12[par], Vh}, in, epi, ra, dored);
+            return run_dslash<S, LinksHv, LinksH12, false>(ctx, par, L, LinksH12{nullptr, Vh}, in, epi, ra, dored);
+        }
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "link precision must be 64, 32 or 16");
     }
-    return set_err(ctx, HISQ_ERR_INVALID_ARG, "FP32 links need FP32 or FP16 vectors");
+    return set_err(ctx, HISQ_ERR_INVALID_ARG, "FP32/FP16 links need FP32 or FP16 vectors");
 }
 
-hisq_status launch_dslash(hisq_ctx *ctx, int out_parity, int prec, int link_prec, const void *in, void *out,
-                          double a, const void *x, double b, const void *y, double c, int norm_slot)
+hisq_status launch_dslash(hisq_ctx *ctx, int out_parity, int prec, int link_prec, const void *in, void *out, double a,
+                          const void *x, double b, const void *y, double c, int norm_slot)
 {
     const int Vh = ctx->g.Vh;
     if (!ctx->links_loaded) return set_err(ctx, HISQ_ERR_STATE, "links not loaded");
+    if ((prec == 64) != (link_prec == 64)) return set_err(ctx, HISQ_ERR_INVALID_ARG, "FP64 vectors go with FP64 links");
     void *xx = const_cast<void *>(x ? x : out), *yy = const_cast<void *>(y ? y : out);
+    RedArgs ra = red_args(ctx, FIN_STORE, norm_slot < 0 ? 0 : norm_slot);
+    const int dored = norm_slot >= 0;
+    auto go = [&](auto in_, auto out_, auto x_, auto y_) -> hisq_status {
+        typedef decltype(in_) S;
+        typedef typename S::real R;
+        EpiXpay<S> epi{out_, x_, y_, R(a), R(b), R(c), x != nullptr, y != nullptr, dored};
+        return run_any(ctx, out_parity, link_prec, in_, epi, ra, dored);
+    };
+    void *ii = const_cast<void *>(in);
     switch (prec) {
-    case 64:
-        if (link_prec != 64) return set_err(ctx, HISQ_ERR_INVALID_ARG, "FP64 vectors need FP64 links");
-        return dslash_prec<SpinorD>(ctx, out_parity, 64, make_spinorD(const_cast<void *>(in), Vh),
-                                    make_spinorD(out, Vh), a, x, b, y, c, norm_slot, make_spinorD(xx, Vh),
-                                    make_spinorD(yy, Vh));
-    case 32:
-        return dslash_prec<SpinorF>(ctx, out_parity, 32, make_spinorF(const_cast<void *>(in), Vh),
-                                    make_spinorF(out, Vh), a, x, b, y, c, norm_slot, make_spinorF(xx, Vh),
-                                    make_spinorF(yy, Vh));
-    case 16:
-        return dslash_prec<SpinorH>(ctx, out_parity, 32, make_spinorH(const_cast<void *>(in), Vh),
-                                    make_spinorH(out, Vh), a, x, b, y, c, norm_slot, make_spinorH(xx, Vh),
-                                    make_spinorH(yy, Vh));
+    case 64: return go(make_spinorD(ii, Vh), make_spinorD(out, Vh), make_spinorD(xx, Vh), make_spinorD(yy, Vh));
+    case 32: return go(make_spinorF(ii, Vh), make_spinorF(out, Vh), make_spinorF(xx, Vh), make_spinorF(yy, Vh));
+    case 16: return go(make_spinorH(ii, Vh), make_spinorH(out, Vh), make_spinorH(xx, Vh), make_spinorH(yy, Vh));
     }
     return set_err(ctx, HISQ_ERR_INVALID_ARG, "precision must be 64, 32 or 16");
 }
@@ -234,26 +285,18 @@ hisq_status launch_cg_dslash_tt(hisq_ctx *ctx, int prec, int link_prec, const vo
 {
     const int Vh = ctx->g.Vh;
     RedArgs ra = red_args(ctx, FIN_CG_ALPHA);
+    void *pp = const_cast<void *>(p);
+    auto go = [&](auto in_, auto out_) -> hisq_status {
+        typedef decltype(in_) S;
+        typedef typename S::real R;
+        EpiXpay<S> epi{out_, out_, out_, R(0), R(0), R(1), 0, 0, 1};
+        return run_any(ctx, 1, link_prec, in_, epi, ra, 1);
+    };
     switch (prec) {
-    case 64: {
-        SpinorD in = make_spinorD(const_cast<void *>(p), Vh), out = make_spinorD(tmp, Vh);
-        EpiXpay<SpinorD> epi{out, out, out, 0.0, 0.0, 1.0, 0, 0, 1};
-        return run_dslash<SpinorD, LinksD, false>(ctx, 1, links_d(ctx, 1), in, epi, ra, 1);
+    case 64: return go(make_spinorD(pp, Vh), make_spinorD(tmp, Vh));
+    case 32: return go(make_spinorF(pp, Vh), make_spinorF(tmp, Vh));
+    case 16: return go(make_spinorH(pp, Vh), make_spinorH(tmp, Vh));
     }
-    case 32: {
-        SpinorF in = make_spinorF(const_cast<void *>(p), Vh), out = make_spinorF(tmp, Vh);
-        EpiXpay<SpinorF> epi{out, out, out, 0.f, 0.f, 1.f, 0, 0, 1};
-        if (ctx->long_recon == 12) return run_dslash<SpinorF, LinksFv, true>(ctx, 1, links_f(ctx, 1), in, epi, ra, 1);
-        return run_dslash<SpinorF, LinksFv, false>(ctx, 1, links_f(ctx, 1), in, epi, ra, 1);
-    }
-    case 16: {
-        SpinorH in = make_spinorH(const_cast<void *>(p), Vh), out = make_spinorH(tmp, Vh);
-        EpiXpay<SpinorH> epi{out, out, out, 0.f, 0.f, 1.f, 0, 0, 1};
-        if (ctx->long_recon == 12) return run_dslash<SpinorH, LinksFv, true>(ctx, 1, links_f(ctx, 1), in, epi, ra, 1);
-        return run_dslash<SpinorH, LinksFv, false>(ctx, 1, links_f(ctx, 1), in, epi, ra, 1);
-    }
-    }
-    (void)link_prec;
     return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad sloppy precision");
 }
 
@@ -264,26 +307,21 @@ hisq_status launch_cg_dslash_update(hisq_ctx *ctx, int prec, int link_prec, int 
 {
     const int Vh = ctx->g.Vh;
     RedArgs ra = red_args(ctx, FIN_CG_BETA);
-    (void)link_prec;
+    void *tt = const_cast<void *>(tmp), *pp = const_cast<void *>(p);
     switch (prec) {
     case 64: {
-        SpinorD in = make_spinorD(const_cast<void *>(tmp), Vh);
-        EpiCG<SpinorD, SpinorD> epi{make_spinorD(const_cast<void *>(p), Vh), make_spinorD(r, Vh), make_spinorD(x, Vh), ctx->scal};
-        return run_dslash<SpinorD, LinksD, false>(ctx, 0, links_d(ctx, 0), in, epi, ra, 1);
+        EpiCG<SpinorD, SpinorD> epi{make_spinorD(pp, Vh), make_spinorD(r, Vh), make_spinorD(x, Vh), ctx->scal};
+        return run_any(ctx, 0, link_prec, make_spinorD(tt, Vh), epi, ra, 1);
     }
     case 32: {
-        SpinorF in = make_spinorF(const_cast<void *>(tmp), Vh);
         if (xprec != 32) return set_err(ctx, HISQ_ERR_INVALID_ARG, "x precision");
-        EpiCG<SpinorF, SpinorF> epi{make_spinorF(const_cast<void *>(p), Vh), make_spinorF(r, Vh), make_spinorF(x, Vh), ctx->scal};
-        if (ctx->long_recon == 12) return run_dslash<SpinorF, LinksFv, true>(ctx, 0, links_f(ctx, 0), in, epi, ra, 1);
-        return run_dslash<SpinorF, LinksFv, false>(ctx, 0, links_f(ctx, 0), in, epi, ra, 1);
+        EpiCG<SpinorF, SpinorF> epi{make_spinorF(pp, Vh), make_spinorF(r, Vh), make_spinorF(x, Vh), ctx->scal};
+        return run_any(ctx, 0, link_prec, make_spinorF(tt, Vh), epi, ra, 1);
     }
     case 16: {
-        SpinorH in = make_spinorH(const_cast<void *>(tmp), Vh);
         if (xprec != 32) return set_err(ctx, HISQ_ERR_INVALID_ARG, "x precision");
-        EpiCG<SpinorH, SpinorF> epi{make_spinorH(const_cast<void *>(p), Vh), make_spinorH(r, Vh), make_spinorF(x, Vh), ctx->scal};
-        if (ctx->long_recon == 12) return run_dslash<SpinorH, LinksFv, true>(ctx, 0, links_f(ctx, 0), in, epi, ra, 1);
-        return run_dslash<SpinorH, LinksFv, false>(ctx, 0, links_f(ctx, 0), in, epi, ra, 1);
+        EpiCG<SpinorH, SpinorF> epi{make_spinorH(pp, Vh), make_spinorH(r, Vh), make_spinorF(x, Vh), ctx->scal};
+        return run_any(ctx, 0, link_prec, make_spinorH(tt, Vh), epi, ra, 1);
     }
     }
     return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad sloppy precision");

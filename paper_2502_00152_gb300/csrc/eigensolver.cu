@@ -247,6 +247,7 @@ static hisq_status store_eigvecs(hisq_ctx *ctx, int n, const void *vf32, int pre
     ctx->eig.vecs = store;
     ctx->eig.n = n;
     ctx->eig.prec = prec;
+    ctx->eig.version++;
     ctx->eig.eps.resize(n);
     if (residuals) residuals->resize(n);
     for (int j = 0; j < n; j++) {

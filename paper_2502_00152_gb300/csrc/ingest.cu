@@ -6,7 +6,7 @@
 //   fwd, n hops:  W = eta_mu(x) * bc(x, n)        * U_mu(x)
 //   bwd, n hops:  W = -eta_mu(x) * bc(x - n mu, n) * U_mu(x - n mu)^dag
 // with bc = -1 for a hop that wraps the time boundary of an antiperiodic
-// lattice.  They are written in FP64 and FP32 (see internal.cuh for layouts).
+// lattice.  They are written in FP64, FP32 and FP16 (see internal.cuh for layouts).
 // With 12-real long links only rows 0 and 1 of S = U_long / long_scale are kept
 // (for fwd and bwd); the Dslash rebuilds row 2 and applies the sign and scale.
 #include "internal.cuh"
@@ -69,8 +69,16 @@ struct IngestOut {
     double2 *d;    // FP64 [mu][kind][fb][k][Vh] for this parity
     float4 *f;     // FP32 [mu][nk][k][Vh]
     float4 *f12;   // FP32 recon-12 long [mu][6][Vh] or null
+    uint2 *h;      // FP16 [mu][nk][k][Vh]
+    uint2 *h12;    // FP16 recon-12 long [mu][6][Vh] or null
     int nk;
 };
+
+__device__ __forceinline__ unsigned pack_half2(double re, double im)
+{
+    __half2 h = __floats2half2_rn(float(re), float(im));
+    return *reinterpret_cast<unsigned *>(&h);
+}
 
 // one thread per (output site cb, mu) of parity `par`
 __global__ void k_ingest(Geom g, int par, const double2 *__restrict__ fat, const double2 *__restrict__ lng,
@@ -123,15 +131,22 @@ __global__ void k_ingest(Geom g, int par, const double2 *__restrict__ fat, const
                 const double dev = fmax(su3_deviation(Sf), su3_deviation(Sb));
                 atomic_max_nonneg(max_dev, isfinite(dev) ? float(dev) : 1e30f);
                 float4 *q = o.f12 + size_t(mu * 6) * Vh + cb;
+                uint2 *qh = o.h12 + size_t(mu * 6) * Vh + cb;
 #pragma unroll
-                for (int k = 0; k < 6; k++)
+                for (int k = 0; k < 6; k++) {
                     __stcs(q + size_t(k) * Vh, make_float4(float(Sf[k].x), float(Sf[k].y), float(Sb[k].x), float(Sb[k].y)));
+                    __stcs(qh + size_t(k) * Vh, make_uint2(pack_half2(Sf[k].x, Sf[k].y), pack_half2(Sb[k].x, Sb[k].y)));
+                }
             } else {
                 float4 *q = o.f + size_t((mu * o.nk + kind) * 9) * Vh + cb;
+                uint2 *qh = o.h + size_t((mu * o.nk + kind) * 9) * Vh + cb;
 #pragma unroll
-                for (int k = 0; k < 9; k++)
+                for (int k = 0; k < 9; k++) {
                     __stcs(q + size_t(k) * Vh, make_float4(float(sf * Mf[k].x), float(sf * Mf[k].y),
                                                            float(sbk * Mb[k].x), float(sbk * Mb[k].y)));
+                    __stcs(qh + size_t(k) * Vh, make_uint2(pack_half2(sf * Mf[k].x, sf * Mf[k].y),
+                                                           pack_half2(sbk * Mb[k].x, sbk * Mb[k].y)));
+                }
             }
         }
     }
@@ -148,7 +163,8 @@ hisq_status ingest_links(hisq_ctx *ctx, const double *fat_dev, const double *lng
     HISQ_CUDA(cudaMemsetAsync(d_dev, 0, sizeof(float) + sizeof(int), ctx->stream));
     const int nk = recon == 12 ? 1 : 2;
     for (int par = 0; par < 2; par++) {
-        IngestOut o{ctx->links_d[par], ctx->links_f[par], recon == 12 ? ctx->links_f12[par] : nullptr, nk};
+        IngestOut o{ctx->links_d[par], ctx->links_f[par], recon == 12 ? ctx->links_f12[par] : nullptr, ctx->links_h[par],
+                    recon == 12 ? ctx->links_h12[par] : nullptr, nk};
         int grid = (4 * Vh + 255) / 256;
         if (grid > ctx->num_sms * 16) grid = ctx->num_sms * 16;
         ctx->launches++;

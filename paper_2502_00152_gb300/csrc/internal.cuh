@@ -277,6 +277,8 @@ __device__ __forceinline__ CVec<To> cvt(const CVec<From> &v)
 // FP32 long links with recon 12: float4 [p][mu][k=0..5][Vh] holding rows 0,1
 //   of the SU(3) factor S of fwd and bwd; W = sign * long_scale * S, with
 //   sign = +-eta_mu(x) * (boundary sign) recomputed from the coordinates.
+// FP16 (recon 18): uint2 [p][mu][kind][k=0..8][Vh], uint2 = (fwd_k, bwd_k) as
+//   two half2; FP16 long links with recon 12: uint2 [p][mu][k=0..5][Vh].
 struct LinksD {
     const double2 *base; // parity offset applied
     int Vh;
@@ -357,6 +359,35 @@ enum FinishOp : int {
 };
 
 constexpr int kMaxRedVals = 8;
+
+// ------------------------------------------------- multi right-hand sides
+constexpr int kMaxBatch = 64;
+
+// per right-hand-side CG scalars of a batched solve (indexed by RHS id)
+struct BatchScalars {
+    double rr[kMaxBatch], rr_new[kMaxBatch], pp[kMaxBatch], tt[kMaxBatch];
+    double alpha[kMaxBatch], beta[kMaxBatch], out[kMaxBatch];
+    double m4;
+    long long iter;
+    int kact;             // active right-hand sides
+    int idx[kMaxBatch];   // slot -> RHS id
+};
+
+enum BatchFinishOp : int {
+    BFIN_STORE = 0, // out[j] = total
+    BFIN_ALPHA = 1, // tt[j] = total; alpha[j] = rr[j] / (m4 pp[j] + tt[j])
+    BFIN_BETA = 2,  // rr_new[j] = total; beta[j] = rr_new[j] / rr[j]; monitor
+    BFIN_P = 3      // pp[j] = total; rr[j] = rr_new[j]; iter += 1
+};
+
+struct BatchRed {
+    double *partials;     // >= gridDim.x * kMaxBatch
+    unsigned int *ticket;
+    BatchScalars *scal;
+    double *monitor;      // host-mapped [monitor_len][kMaxBatch]
+    int monitor_len;
+    int op;
+};
 constexpr int kRedThreads = 256;
 
 struct RedArgs {
@@ -467,6 +498,17 @@ enum BufId : int {
     BUF_EPS,           // eigenvalues on the device (FP64)
     BUF_EIG_Y,         // Ritz rotation matrix (FP64)
     BUF_EIG_W,         // eigensolver work vectors
+    BUF_B_Y,           // batched solve: k FP64 right-hand sides y_e
+    BUF_B_XHI,
+    BUF_B_RHI,
+    BUF_B_XSL,
+    BUF_B_RSL,
+    BUF_B_P,
+    BUF_B_TMP,
+    BUF_TC_WORK,       // tensor-core deflation: R' operands, scales, status
+    BUF_TC_PART,       // projection partial tiles per K split
+    BUF_TC_C,          // projected coefficients (FP64)
+    BUF_TC_D,          // expansion operands
     BUF_COUNT
 };
 
@@ -475,6 +517,7 @@ struct EigenStore {
     int prec = 32;        // storage precision (32 or 16)
     void *vecs = nullptr; // n vectors of spinor_bytes(prec, Vh)
     std::vector<double> eps; // massless eigenvalues, ascending
+    unsigned version = 0;    // bumped whenever the stored pairs change
 };
 
 } // namespace hisq
@@ -498,6 +541,8 @@ struct hisq_ctx {
     double2 *links_d[2] = {nullptr, nullptr};  // FP64, 16 hops
     float4 *links_f[2] = {nullptr, nullptr};   // FP32: fat (+ long when recon 18)
     float4 *links_f12[2] = {nullptr, nullptr}; // FP32 long, recon 12
+    uint2 *links_h[2] = {nullptr, nullptr};    // FP16: fat (+ long when recon 18)
+    uint2 *links_h12[2] = {nullptr, nullptr};  // FP16 long, recon 12
 
     // reduction scratch
     double *partials = nullptr;
@@ -509,6 +554,13 @@ struct hisq_ctx {
     int max_red_blocks = 0;
 
     hisq::EigenStore eig;
+
+    // batched solves
+    hisq::BatchScalars *bscal = nullptr;
+    double *bpartials = nullptr;
+    double *bmonitor_h = nullptr; // host-mapped
+    double *bmonitor_d = nullptr;
+    int bmonitor_len = 4096;
 
     // scratch buffers (grown on demand)
     void *bufs[hisq::BUF_COUNT] = {};
@@ -602,6 +654,12 @@ hisq_status launch_random_f(hisq_ctx *ctx, unsigned long long seed, void *out);
 // basis rotation for the eigensolver: out_j = sum_i Y[i][j] in_i, real Y (k_in x k_out)
 hisq_status launch_rotate(hisq_ctx *ctx, int k_in, int k_out, const void *Vin, const double *Y_dev,
                           void *Vout);
+
+// batched operator (mrhs.cu): active right-hand sides from ctx->bscal->idx
+hisq_status launch_mrhs_dslash_tt(hisq_ctx *ctx, int prec, int link_prec, void *p, void *tmp, int kact);
+hisq_status launch_mrhs_dslash_update(hisq_ctx *ctx, int prec, int link_prec, void *tmp, void *p, void *x, void *r,
+                                      int kact);
+hisq_status launch_mrhs_p_update(hisq_ctx *ctx, int prec, void *r, void *p, int kact);
 
 // link ingest (ingest.cu)
 hisq_status ingest_links(hisq_ctx *ctx, const double *fat_dev, const double *lng_dev, int recon,

@@ -8,6 +8,7 @@
 // The host drives the iterations with a one-iteration lag: it queues iteration
 // k and only then reads the residual of iteration k-1 from mapped memory, so the
 // GPU never idles waiting for the host.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -24,6 +25,10 @@ hisq_status read_slots(hisq_ctx *ctx, int slot0, int n, double *out);
         hisq_status s_ = (x);                   \
         if (s_ != HISQ_OK) return s_;           \
     } while (0)
+
+// force a reliable update when the sloppy residual has not triggered one for
+// this many iterations (it can stall when the sloppy operator is too coarse)
+constexpr long long kMaxItersBetweenUpdates = 1000;
 
 enum Slot { SL_YNORM = 0, SL_ETAE = 1, SL_ETAO = 2, SL_RHI = 3, SL_RE = 4, SL_RO = 5, SL_PP = 6 };
 
@@ -44,6 +49,30 @@ hisq_status deflate_add(hisq_ctx *ctx, int n, const double *r, double *x)
     TRY(launch_defl_project(ctx, n, ctx->eig.prec, ctx->eig.vecs, 64, r, c));
     TRY(launch_defl_scale(ctx, n, c, eps, 4.0 * ctx->mass * ctx->mass));
     return launch_defl_expand(ctx, n, ctx->eig.prec, ctx->eig.vecs, c, 1.0, 64, x);
+}
+
+hisq_status launch_defl_expand2(hisq_ctx *ctx, int n, int vprec, const void *V, const double *c_dev,
+                                const double *eps_dev, double shift, double *x, double *r);
+
+// Deflation step on the pair (x, r = b - A x): c = V^dag r, x += V Lambda^-1 c,
+// r -= V c (Eq. 4 applied to the current residual).  The new residual follows
+// from A v_i = lambda_i v_i of the stored pairs instead of an FP64 operator
+// application; the next reliable update recomputes it exactly.  |r|^2 -> slot.
+static hisq_status deflate_pair(hisq_ctx *ctx, int n, const double *b, double *r, double *x, double *t_odd, int slot)
+{
+    // beyond the fused kernel, or with FP16 eigenvectors (whose rounding, divided
+    // by small lambda_i, breaks A V Lambda^-1 c = V c): x update, then the FP64
+    // residual
+    if (n > 4096 || ctx->eig.prec != 32) {
+        TRY(deflate_add(ctx, n, r, x));
+        return residual_hi(ctx, b, x, r, t_odd, slot);
+    }
+    double *eps = eig_eps_dev(ctx);
+    double *c = (double *)get_buf(ctx, BUF_DEFL_C, sizeof(double) * 2 * (n > 0 ? n : 1));
+    if (!eps || !c) return set_err(ctx, HISQ_ERR_OOM, "deflation buffers");
+    TRY(launch_defl_project(ctx, n, ctx->eig.prec, ctx->eig.vecs, 64, r, c));
+    TRY(launch_defl_expand2(ctx, n, ctx->eig.prec, ctx->eig.vecs, c, eps, 4.0 * ctx->mass * ctx->mass, x, r));
+    return launch_norm2(ctx, 64, r, slot);
 }
 
 struct HostScalars {
@@ -71,7 +100,7 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
 {
     const int Vh = ctx->g.Vh;
     const int prec = P->precision_sloppy;
-    const int lprec = prec == 64 ? 64 : 32;
+    const int lprec = prec == 64 ? 64 : P->link_precision_sloppy;
     const int xprec = prec == 64 ? 64 : 32;
     double *r_hi = (double *)get_buf(ctx, BUF_RHI, spinor_bytes(64, Vh));
     double *t_hi = (double *)get_buf(ctx, BUF_TMPHI, spinor_bytes(64, Vh));
@@ -137,6 +166,9 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
     };
 
     double r_last = rt, r_defl = rt;
+    double r_best = rt, rn_last_seen = rt;
+    int no_progress = 0; // reliable updates in a row without halving the best true residual
+    long long last_update_it = 0;
     long long k = 0, checked = 0;
     const long long maxit = P->max_iter > 0 ? P->max_iter : 1;
     hisq_status result = HISQ_ERR_NOT_CONVERGED;
@@ -165,7 +197,12 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
                 return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite residual at iteration %lld", j);
             }
             const double rn = std::sqrt(rr);
-            if (rn < target || rn < P->delta_rd * r_last) update = true;
+            rn_last_seen = rn;
+            // a sloppy residual that grows far above the last true one means the
+            // sloppy recurrence has lost contact: replace it now
+            if (rn < target || rn < P->delta_rd * r_last || rn > 1e3 * r_last) update = true;
+            // a sloppy residual that stops falling also needs the true one
+            if (j - last_update_it >= kMaxItersBetweenUpdates) update = true;
             checked = j + 1;
             retire(j + 1);
         }
@@ -178,9 +215,12 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
         double r2 = 0;
         TRY(read_slots(ctx, SL_RHI, 1, &r2));
         if (!std::isfinite(r2)) return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite true residual");
+        if (log_level() > 1)
+            fprintf(stderr, "[hisq] cg it %lld: iterated |r| %.4e\n", k, rn_last_seen);
         rt = std::sqrt(r2);
         st->reliable_updates++;
         checked = k;
+        last_update_it = k;
         if (log_level() > 0)
             fprintf(stderr, "[hisq] cg it %lld: reliable update, true |r| %.4e (target %.4e)\n", k, rt, target);
         if (rt <= target) {
@@ -188,12 +228,23 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
             break;
         }
         if (force) break;
-        bool restart = false;
+        // stagnation: the sloppy operator is too far from the FP64 one for this
+        // spectrum (its error exceeds the smallest eigenvalue); give up cleanly
+        if (rt < 0.5 * r_best) {
+            r_best = rt;
+            no_progress = 0;
+        } else if (++no_progress >= 8) {
+            set_err(ctx, HISQ_ERR_NOT_CONVERGED, "stagnation: %d reliable updates without progress (true |r| %.3e)",
+                    no_progress, rt);
+            break;
+        }
+        // restart the search direction when the true residual is far from the
+        // iterated one (the kept direction would no longer be conjugate)
+        bool restart = rt > 10.0 * rn_last_seen;
         if (n_defl > 0 && P->delta_tr > 0 && rt < P->delta_tr * r_defl) {
             HISQ_CUDA(cudaEventRecord(d0, ctx->stream));
-            TRY(deflate_add(ctx, n_defl, r_hi, x));
+            TRY(deflate_pair(ctx, n_defl, b, r_hi, x, t_hi, SL_RHI));
             HISQ_CUDA(cudaEventRecord(d1, ctx->stream));
-            TRY(residual_hi(ctx, b, x, r_hi, t_hi, SL_RHI));
             TRY(read_slots(ctx, SL_RHI, 1, &r2));
             float ms = 0;
             cudaEventElapsedTime(&ms, d0, d1);
@@ -272,15 +323,15 @@ hisq_status solve_one(hisq_ctx *ctx, const hisq_solve_params *P, const double *e
         n_defl = P->n_defl > 0 ? std::min(P->n_defl, ctx->eig.n) : ctx->eig.n;
     }
     double defl_s = 0;
+    // x = 0, r = y; with deflation x = V Lambda^-1 V^dag y, r = y - V V^dag y
+    HISQ_CUDA(cudaMemcpyAsync(r_hi, y, spinor_bytes(64, Vh), cudaMemcpyDeviceToDevice, ctx->stream));
+    double r2 = nrm[0];
     if (n_defl > 0) {
         auto d0 = std::chrono::steady_clock::now();
-        TRY(deflate_add(ctx, n_defl, y, x));
-        HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+        TRY(deflate_pair(ctx, n_defl, y, r_hi, x, t_hi, SL_RHI));
+        TRY(read_slots(ctx, SL_RHI, 1, &r2));
         defl_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - d0).count();
     }
-    TRY(residual_hi(ctx, y, x, r_hi, t_hi, SL_RHI));
-    double r2 = 0;
-    TRY(read_slots(ctx, SL_RHI, 1, &r2));
 
     // (a6) CG with reliable updates
     double rfin = 0;
@@ -313,9 +364,20 @@ static hisq_status check_solve_args(hisq_ctx *ctx, const hisq_solve_params *P, i
     if (!(ctx->mass > 0)) return set_err(ctx, HISQ_ERR_STATE, "mass not set");
     if (P->precision_sloppy != 64 && P->precision_sloppy != 32 && P->precision_sloppy != 16)
         return set_err(ctx, HISQ_ERR_INVALID_ARG, "precision_sloppy must be 64, 32 or 16");
+    if (P->precision_sloppy != 64 && P->link_precision_sloppy != 32 && P->link_precision_sloppy != 16)
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "link_precision_sloppy must be 32 or 16");
     if (!(P->tol > 0) || !(P->delta_rd > 0 && P->delta_rd < 1) || P->delta_tr < 0 || P->delta_tr >= 1)
         return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad tolerance / delta parameters");
     return HISQ_OK;
+}
+
+hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const double *eta, double *psi, int k,
+                          hisq_solve_stats *stats);
+
+static bool use_batched(const hisq_solve_params *P, int nrhs)
+{
+    return P->batch && nrhs > 1 && (P->precision_sloppy == 32 || P->precision_sloppy == 16) &&
+           P->link_precision_sloppy == 32;
 }
 
 } // namespace hisq
@@ -330,12 +392,36 @@ hisq_status hisq_solve(hisq_ctx *ctx, const double *eta, double *psi, int nrhs, 
     if (!ctx) return HISQ_ERR_INVALID_ARG;
     if (!eta || !psi) return set_err(ctx, HISQ_ERR_INVALID_ARG, "null field");
     TRY(check_solve_args(ctx, params, nrhs));
+    ctx->err.clear();
     HISQ_CUDA(cudaSetDevice(ctx->device));
     const size_t bytes = size_t(ctx->g.V) * 48;
+    hisq_status worst = HISQ_OK;
+    if (use_batched(params, nrhs)) {
+        for (int k0 = 0; k0 < nrhs; k0 += kMaxBatch) {
+            const int kb = std::min(kMaxBatch, nrhs - k0);
+            double *de = (double *)get_buf(ctx, BUF_ETA_FULL, bytes * kb);
+            double *dp = (double *)get_buf(ctx, BUF_PSI_FULL, bytes * kb);
+            if (!de || !dp) return HISQ_ERR_OOM;
+            auto t0 = std::chrono::steady_clock::now();
+            HISQ_CUDA(cudaMemcpyAsync(de, eta + size_t(k0) * ctx->g.V * 6, bytes * kb, cudaMemcpyHostToDevice, ctx->stream));
+            hisq_status s = solve_batched(ctx, params, de, dp, kb, stats ? stats + k0 : nullptr);
+            if (s != HISQ_OK && s != HISQ_ERR_NOT_CONVERGED) return s;
+            HISQ_CUDA(cudaMemcpyAsync(psi + size_t(k0) * ctx->g.V * 6, dp, bytes * kb, cudaMemcpyDeviceToHost, ctx->stream));
+            HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+            const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            if (stats)
+                for (int j = 0; j < kb; j++) stats[k0 + j].seconds_total = secs / kb;
+            if (s != HISQ_OK) worst = s;
+        }
+        if (worst != HISQ_OK) {
+        const std::string why = ctx->err;
+        set_err(ctx, worst, "at least one right-hand side did not converge (%s)", why.c_str());
+    }
+        return worst;
+    }
     double *de = (double *)get_buf(ctx, BUF_ETA_FULL, bytes);
     double *dp = (double *)get_buf(ctx, BUF_PSI_FULL, bytes);
     if (!de || !dp) return HISQ_ERR_OOM;
-    hisq_status worst = HISQ_OK;
     for (int k = 0; k < nrhs; k++) {
         hisq_solve_stats st;
         auto t0 = std::chrono::steady_clock::now();
@@ -348,7 +434,10 @@ hisq_status hisq_solve(hisq_ctx *ctx, const double *eta, double *psi, int nrhs, 
         if (stats) stats[k] = st;
         if (s != HISQ_OK) worst = s;
     }
-    if (worst != HISQ_OK) set_err(ctx, worst, "at least one right-hand side did not converge");
+    if (worst != HISQ_OK) {
+        const std::string why = ctx->err;
+        set_err(ctx, worst, "at least one right-hand side did not converge (%s)", why.c_str());
+    }
     return worst;
 }
 
@@ -365,8 +454,23 @@ hisq_status hisq_solve_device(hisq_ctx *ctx, const double *eta_dev, double *psi_
     if (!ctx) return HISQ_ERR_INVALID_ARG;
     if (!eta_dev || !psi_dev) return set_err(ctx, HISQ_ERR_INVALID_ARG, "null field");
     TRY(check_solve_args(ctx, params, nrhs));
+    ctx->err.clear();
     HISQ_CUDA(cudaSetDevice(ctx->device));
     hisq_status worst = HISQ_OK;
+    if (use_batched(params, nrhs)) {
+        for (int k0 = 0; k0 < nrhs; k0 += kMaxBatch) {
+            const int kb = std::min(kMaxBatch, nrhs - k0);
+            hisq_status s = solve_batched(ctx, params, eta_dev + size_t(k0) * ctx->g.V * 6,
+                                          psi_dev + size_t(k0) * ctx->g.V * 6, kb, stats ? stats + k0 : nullptr);
+            if (s != HISQ_OK && s != HISQ_ERR_NOT_CONVERGED) return s;
+            if (s != HISQ_OK) worst = s;
+        }
+        if (worst != HISQ_OK) {
+        const std::string why = ctx->err;
+        set_err(ctx, worst, "at least one right-hand side did not converge (%s)", why.c_str());
+    }
+        return worst;
+    }
     for (int k = 0; k < nrhs; k++) {
         hisq_solve_stats st;
         hisq_status s = solve_one(ctx, params, eta_dev + size_t(k) * ctx->g.V * 6, psi_dev + size_t(k) * ctx->g.V * 6, &st);
@@ -374,7 +478,10 @@ hisq_status hisq_solve_device(hisq_ctx *ctx, const double *eta_dev, double *psi_
         if (stats) stats[k] = st;
         if (s != HISQ_OK) worst = s;
     }
-    if (worst != HISQ_OK) set_err(ctx, worst, "at least one right-hand side did not converge");
+    if (worst != HISQ_OK) {
+        const std::string why = ctx->err;
+        set_err(ctx, worst, "at least one right-hand side did not converge (%s)", why.c_str());
+    }
     return worst;
 }
 

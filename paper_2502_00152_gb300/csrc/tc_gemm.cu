@@ -1,0 +1,603 @@
+// tc_gemm.cu -- the deflation projection and expansion of a batch of right-hand
+// sides as complex GEMMs on the 5th-generation tensor cores (tcgen05, FP16
+// operands, FP32 accumulation in tensor memory, TMA-fed shared memory).
+// Eq. 4 of the paper for k right-hand sides at once:
+//   C = V^dag R   (n x k),   X += V Lambda^-1 C,   R -= V C.
+//
+// Complex -> real: with V stored as interleaved (re, im) FP16 and
+//   R'_{2j} = (Re r_j, Im r_j),  R'_{2j+1} = (Im r_j, -Re r_j)
+// the real product V R'^T gives (Re c_ij, Im c_ij) in columns (2j, 2j+1).  The
+// expansion uses the site-major copy of V, rows s, K = (i, re/im), against
+// D'_{4j..4j+3} built from d = c / lambda and c, so one GEMM updates x and r.
+// Every operand is split into an FP16 high part and an FP16 residual part and
+// three MMAs (hi*hi + hi*lo + lo*hi) are accumulated, which gives about 22
+// significant bits: enough for the updated residual to stay consistent with
+// the updated solution (r -= V c uses A v_i = lambda_i v_i).
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "internal.cuh"
+#include "tc.cuh"
+
+namespace hisq {
+
+hisq_status read_slots(hisq_ctx *ctx, int slot0, int n, double *out);
+
+#define TRY_HISQ(x)                             \
+    do {                                        \
+        hisq_status s_ = (x);                   \
+        if (s_ != HISQ_OK) return s_;           \
+    } while (0)
+
+constexpr int TC_BK = 64;   // K elements per stage (128 B of FP16)
+constexpr int TC_ROWB = 128; // bytes per swizzled row
+
+// ------------------------------------------------------------- tensor maps
+typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                       const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                       CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static PFN_encodeTiled_t encode_fn()
+{
+    static std::once_flag once;
+    static PFN_encodeTiled_t fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_encodeTiled_t>(p);
+    });
+    return fn;
+}
+
+// 2D FP16 tensor: inner dimension `inner` elements (contiguous), `rows` rows of
+// `row_bytes`; box {64, box_rows}, 128-byte swizzle, zero fill out of bounds.
+static bool make_tmap(CUtensorMap *tm, const void *base, uint64_t inner, uint64_t rows, uint64_t row_bytes,
+                      uint32_t box_rows)
+{
+    PFN_encodeTiled_t enc = encode_fn();
+    if (!enc) return false;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (row_bytes & 15) || box_rows == 0 || box_rows > 256) return false;
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {row_bytes};
+    cuuint32_t box[2] = {uint32_t(TC_BK), box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// ------------------------------------------------------------- the GEMM kernel
+// D[m][nn] = sum_k A[m][k] B[nn][k] over this CTA's K range for MT row tiles of
+// 128 and N columns, operands split into hi/lo FP16 tensors (4 maps).
+//   mode 0 (projection): blockIdx.x = K split, rows m0 = blockIdx.y * MT * 128;
+//            the FP32 tile is written to part[split][m][nn].
+//   mode 1 (expansion):  persistent over row tiles (MT = 1), full K range; the
+//            epilogue applies the result to the right-hand-side fields.
+struct ExpandEpi {
+    double2 *x;       // k FP64 even fields, element s of field j at x + j*xs + s
+    double2 *r;
+    size_t fstride;   // double2 elements between fields
+    const float *scale; // 4 per right-hand side: x re/im, r re/im column factors
+    int k;
+    int rows;         // L = 3 Vh
+};
+
+// Warp roles (192 threads): warp 0 issues the TMA loads, warp 1 issues the MMAs
+// and owns the TMEM allocation, warps 2..5 read the accumulator (warp w may
+// only access TMEM lanes 32 * (w % 4) .. +31, so these four cover all 128 rows).
+constexpr int TC_THREADS = 192;
+
+template <int MT, int N, int STAGES, int MODE>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+              const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int K, int kchunk,
+              int Mrows, float *part, ExpandEpi epi, int *status)
+{
+    constexpr int A_TILE = 128 * TC_ROWB;               // 16 KB per 128-row tile
+    constexpr int B_TILE = N * TC_ROWB;
+    constexpr int STAGE = 2 * MT * A_TILE + 2 * B_TILE; // hi + lo
+    constexpr int NCOLS = (MT * N <= 32) ? 32 : (MT * N <= 64) ? 64 : (MT * N <= 128) ? 128 : (MT * N <= 256) ? 256 : 512;
+    constexpr uint32_t IDESC = tc::idesc_f16_f32(128, N);
+    static_assert(N % 16 == 0 && N >= 16 && N <= 256, "N");
+    static_assert(MT * N <= 512, "TMEM columns");
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE);
+    uint64_t *empty = full + STAGES;
+    uint64_t *done = empty + STAGES;     // MMAs of a tile finished
+    uint64_t *drained = done + 1;        // epilogue has read the accumulator
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(drained + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(done, 1);
+        tc::mbar_init(drained, 128);
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) tc::tmem_alloc(tmem_holder, NCOLS);
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t taddr = *tmem_holder;
+
+    // work list: (row tile, K range)
+    int ntiles, tile0, tstride, kbeg, kend;
+    if (MODE == 0) {
+        ntiles = 1;
+        tile0 = blockIdx.y;
+        tstride = 1;
+        kbeg = blockIdx.x * kchunk;
+        kend = min(K, kbeg + kchunk);
+    } else {
+        ntiles = (Mrows + 127) / 128;
+        tile0 = blockIdx.x;
+        tstride = gridDim.x;
+        kbeg = 0;
+        kend = K;
+    }
+    const int nk = (kend - kbeg + TC_BK - 1) / TC_BK;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer
+        tc::prefetch_tmap(&tmAh);
+        tc::prefetch_tmap(&tmAl);
+        tc::prefetch_tmap(&tmBh);
+        tc::prefetch_tmap(&tmBl);
+        uint32_t it = 0;
+        for (int t = tile0; t < (MODE == 0 ? tile0 + 1 : ntiles); t += tstride) {
+            const int m0 = (MODE == 0) ? t * MT * 128 : t * 128;
+            for (int kk = 0; kk < nk; kk++, it++) {
+                const int s = it % STAGES;
+                if (it >= STAGES && !tc::mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, status, tc::TC_TIMEOUT_EMPTY))
+                    goto producer_done;
+                uint8_t *st = smem + s * STAGE;
+                tc::mbar_arrive_expect_tx(&full[s], STAGE);
+                const int kx = kbeg + kk * TC_BK;
+                for (int mt = 0; mt < MT; mt++) {
+                    tc::tma_load_2d(st + mt * A_TILE, &tmAh, &full[s], kx, m0 + mt * 128);
+                    tc::tma_load_2d(st + (MT + mt) * A_TILE, &tmAl, &full[s], kx, m0 + mt * 128);
+                }
+                tc::tma_load_2d(st + 2 * MT * A_TILE, &tmBh, &full[s], kx, 0);
+                tc::tma_load_2d(st + 2 * MT * A_TILE + B_TILE, &tmBl, &full[s], kx, 0);
+            }
+        }
+    producer_done:
+        // the loads of the last stages must have landed before the CTA exits
+        // (already true on the normal path; bounded if the pipeline broke)
+        for (uint32_t j = (it > STAGES ? it - STAGES : 0); j < it; j++)
+            if (!tc::mbar_try_wait(&full[j % STAGES], (j / STAGES) & 1))
+                for (int spin = 0; spin < (1 << 20) && !tc::mbar_try_wait(&full[j % STAGES], (j / STAGES) & 1); spin++) {
+                }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer
+        uint32_t it = 0, tcount = 0;
+        for (int t = tile0; t < (MODE == 0 ? tile0 + 1 : ntiles); t += tstride, tcount++) {
+            if (tcount > 0 && !tc::mbar_wait(drained, (tcount - 1) & 1, status, tc::TC_TIMEOUT_DONE)) break;
+            tc::tc_fence_after();
+            for (int kk = 0; kk < nk; kk++, it++) {
+                const int s = it % STAGES;
+                if (!tc::mbar_wait(&full[s], (it / STAGES) & 1, status, tc::TC_TIMEOUT_FULL)) goto mma_done;
+                tc::tc_fence_after();
+                const uint32_t st = tc::smem_addr(smem + s * STAGE);
+                const uint32_t bh = st + 2 * MT * A_TILE, bl = bh + B_TILE;
+#pragma unroll
+                for (int mt = 0; mt < MT; mt++) {
+                    const uint32_t ah = st + mt * A_TILE, al = st + (MT + mt) * A_TILE;
+#pragma unroll
+                    for (int q = 0; q < TC_BK / 16; q++) {
+                        const uint32_t off = q * 32; // 16 FP16 along K inside the swizzle atom
+                        const uint32_t d = taddr + mt * N;
+                        const uint32_t acc0 = (kk > 0 || q > 0) ? 1u : 0u;
+                        tc::mma_f16(d, tc::smem_desc_sw128(ah + off), tc::smem_desc_sw128(bh + off), IDESC, acc0);
+                        tc::mma_f16(d, tc::smem_desc_sw128(ah + off), tc::smem_desc_sw128(bl + off), IDESC, 1u);
+                        tc::mma_f16(d, tc::smem_desc_sw128(al + off), tc::smem_desc_sw128(bh + off), IDESC, 1u);
+                    }
+                }
+                tc::mma_commit(&empty[s]);
+            }
+            tc::mma_commit(done);
+        }
+    mma_done:;
+    }
+
+    // ---------------- epilogue (warps 2..5)
+    if (warp >= 2) {
+        const int quarter = warp & 3;
+        uint32_t tcount = 0;
+        for (int t = tile0; t < (MODE == 0 ? tile0 + 1 : ntiles); t += tstride, tcount++) {
+            bool ok = tc::mbar_wait(done, tcount & 1, status, tc::TC_TIMEOUT_DONE);
+            tc::tc_fence_after();
+            const int row = quarter * 32 + lane;
+            if (MODE == 0) {
+                for (int mt = 0; mt < MT; mt++) {
+                    const int m = t * MT * 128 + mt * 128 + row;
+#pragma unroll
+                    for (int c0 = 0; c0 < N; c0 += 16) {
+                        float v[16];
+                        tc::tmem_ld16(taddr + (uint32_t(quarter * 32) << 16) + mt * N + c0, v);
+                        if (ok && nk > 0 && m < Mrows) {
+                            float *dst = part + (size_t(blockIdx.x) * Mrows + m) * N + c0;
+#pragma unroll
+                            for (int i = 0; i < 16; i++) dst[i] = v[i];
+                        }
+                    }
+                }
+            } else {
+                const int s = t * 128 + row;
+                for (int c0 = 0; c0 < N; c0 += 16) {
+                    float v[16];
+                    tc::tmem_ld16(taddr + (uint32_t(quarter * 32) << 16) + c0, v);
+                    if (ok && s < epi.rows) {
+#pragma unroll
+                        for (int i = 0; i < 16; i += 4) {
+                            const int j = (c0 + i) >> 2;
+                            if (j < epi.k) {
+                                const float *sc = epi.scale + 4 * j;
+                                double2 *xp = epi.x + epi.fstride * j + s;
+                                double2 *rp = epi.r + epi.fstride * j + s;
+                                double2 xv = *xp, rv = *rp;
+                                xv.x += double(v[i + 0]) * sc[0];
+                                xv.y += double(v[i + 1]) * sc[1];
+                                rv.x -= double(v[i + 2]) * sc[2];
+                                rv.y -= double(v[i + 3]) * sc[3];
+                                *xp = xv;
+                                *rp = rv;
+                            }
+                        }
+                    }
+                }
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(drained);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(taddr, NCOLS);
+    }
+}
+
+// ------------------------------------------------------------- operand builders
+// V (n stored FP32 even fields) -> FP16 hi/lo copies scaled by sigma:
+//   vector-major  [i][s][re,im]   (projection A)
+//   site-major    [s][i][re,im]   (expansion A, row pitch ld_sm halves)
+__global__ void k_build_v(int Vh, int n, const char *__restrict__ V32, size_t vstride, float sigma, __half *vm_hi,
+                          __half *vm_lo, __half *sm_hi, __half *sm_lo, size_t ld_sm)
+{
+    const size_t L = size_t(3) * Vh;
+    const size_t total = L * n;
+    for (size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += size_t(gridDim.x) * blockDim.x) {
+        const int i = int(t / L);
+        const size_t s = t % L; // s = c * Vh + cb
+        const int c = int(s / Vh), cb = int(s % Vh);
+        const char *p = V32 + vstride * i;
+        float re, im;
+        if (c < 2) {
+            const float4 a = reinterpret_cast<const float4 *>(p)[cb];
+            re = c == 0 ? a.x : a.z;
+            im = c == 0 ? a.y : a.w;
+        } else {
+            const float2 b = reinterpret_cast<const float2 *>(p + size_t(Vh) * 16)[cb];
+            re = b.x;
+            im = b.y;
+        }
+        re *= sigma;
+        im *= sigma;
+        const __half hr = __float2half_rn(re), hi_ = __float2half_rn(im);
+        const __half lr = __float2half_rn(re - __half2float(hr)), li = __float2half_rn(im - __half2float(hi_));
+        const size_t vm = (size_t(i) * L + s) * 2, sm = s * ld_sm + size_t(i) * 2;
+        vm_hi[vm] = hr;
+        vm_hi[vm + 1] = hi_;
+        vm_lo[vm] = lr;
+        vm_lo[vm + 1] = li;
+        sm_hi[sm] = hr;
+        sm_hi[sm + 1] = hi_;
+        sm_lo[sm] = lr;
+        sm_lo[sm + 1] = li;
+    }
+}
+
+// R' columns 2j = (Re r_j, Im r_j), 2j+1 = (Im r_j, -Re r_j), times scale[j], hi/lo
+__global__ void k_build_r(int L, int k, const double2 *__restrict__ R, size_t fstride, const float *scale, __half *rh,
+                          __half *rl)
+{
+    const size_t total = size_t(L) * k;
+    for (size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += size_t(gridDim.x) * blockDim.x) {
+        const int j = int(t / L);
+        const size_t s = t % L;
+        const double2 v = R[fstride * j + s];
+        const float a = float(v.x * scale[j]), b = float(v.y * scale[j]);
+        const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
+        const __half la = __float2half_rn(a - __half2float(ha)), lb = __float2half_rn(b - __half2float(hb));
+        const size_t c0 = (size_t(2 * j) * L + s) * 2, c1 = (size_t(2 * j + 1) * L + s) * 2;
+        rh[c0] = ha;
+        rh[c0 + 1] = hb;
+        rl[c0] = la;
+        rl[c0 + 1] = lb;
+        rh[c1] = hb;
+        rh[c1 + 1] = __hneg(ha);
+        rl[c1] = lb;
+        rl[c1 + 1] = __hneg(la);
+    }
+}
+
+// C[i][col] = sum_split part[split][i][col] (fixed order), col < ncol
+__global__ void k_reduce_part(int nsplit, int n, int N, int ncol, const float *__restrict__ part, double *C)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * ncol; t += gridDim.x * blockDim.x) {
+        const int i = t / ncol, col = t % ncol;
+        double s = 0;
+        for (int p = 0; p < nsplit; p++) s += part[(size_t(p) * n + i) * N + col];
+        C[t] = s;
+    }
+}
+
+// ------------------------------------------------------------- host driver
+struct TcState {
+    unsigned version = ~0u;     // eigenpair version the copies were built from
+    int n = 0, Vh = 0;
+    __half *vm_hi = nullptr, *vm_lo = nullptr, *sm_hi = nullptr, *sm_lo = nullptr;
+    size_t ld_sm = 0;
+    size_t bytes = 0;
+    float sigma = 1;
+};
+
+static TcState &tc_state(hisq_ctx *ctx)
+{
+    // one state per context, kept in a side table keyed by the context pointer
+    static std::mutex mu;
+    static std::vector<std::pair<hisq_ctx *, TcState>> table;
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto &e : table)
+        if (e.first == ctx) return e.second;
+    table.emplace_back(ctx, TcState{});
+    return table.back().second;
+}
+
+void tc_release(hisq_ctx *ctx)
+{
+    TcState &S = tc_state(ctx);
+    if (S.vm_hi) dev_free(ctx, S.vm_hi, S.bytes);
+    S = TcState{};
+}
+
+// forget the context's state (called when the context is destroyed)
+void tc_forget(hisq_ctx *ctx)
+{
+    tc_release(ctx);
+}
+
+static hisq_status tc_prepare_v(hisq_ctx *ctx, int n)
+{
+    TcState &S = tc_state(ctx);
+    const int Vh = ctx->g.Vh;
+    if (S.version == ctx->eig.version && S.n == n && S.Vh == Vh && S.vm_hi) return HISQ_OK;
+    if (ctx->eig.prec != 32) return set_err(ctx, HISQ_ERR_INVALID_ARG, "tensor-core deflation needs FP32 eigenvectors");
+    tc_release(ctx);
+    const size_t L = size_t(3) * Vh;
+    const size_t ld_sm = ((size_t(2) * n + 63) / 64) * 64; // halves per site-major row (128 B multiple)
+    const size_t vm = L * n * 2, sm = L * ld_sm;
+    const size_t bytes = (2 * vm + 2 * sm) * sizeof(__half);
+    __half *base = (__half *)dev_alloc(ctx, bytes);
+    if (!base) return HISQ_ERR_OOM;
+    HISQ_CUDA(cudaMemsetAsync(base, 0, bytes, ctx->stream));
+    S.vm_hi = base;
+    S.vm_lo = base + vm;
+    S.sm_hi = base + 2 * vm;
+    S.sm_lo = base + 2 * vm + sm;
+    S.ld_sm = ld_sm;
+    S.bytes = bytes;
+    S.n = n;
+    S.Vh = Vh;
+    S.version = ctx->eig.version;
+    S.sigma = float(std::sqrt(double(L)));
+    ctx->launches++;
+    k_build_v<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(Vh, n, (const char *)ctx->eig.vecs, spinor_bytes(32, Vh),
+                                                          S.sigma, S.vm_hi, S.vm_lo, S.sm_hi, S.sm_lo, ld_sm);
+    HISQ_CUDA(cudaGetLastError());
+    return HISQ_OK;
+}
+
+template <int MT, int N, int ST, int MODE>
+static hisq_status launch_gemm(hisq_ctx *ctx, dim3 grid, const CUtensorMap *m, int K, int kchunk, int Mrows, float *part,
+                               ExpandEpi epi, int *status)
+{
+    constexpr int STAGE = 2 * MT * 128 * TC_ROWB + 2 * N * TC_ROWB;
+    const size_t smem = size_t(ST) * STAGE + 1024 + 256;
+    auto kern = k_tc_gemm<MT, N, ST, MODE>;
+    static bool attr = false;
+    if (!attr) {
+        HISQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+        attr = true;
+    }
+    ctx->launches++;
+    kern<<<grid, TC_THREADS, smem, ctx->stream>>>(m[0], m[1], m[2], m[3], K, kchunk, Mrows, part, epi, status);
+    HISQ_CUDA(cudaGetLastError());
+    return HISQ_OK;
+}
+
+// Batched deflation of k right-hand sides with the first n stored eigenpairs:
+// x_j += sum_i v_i c_ij / lambda_i, r_j -= sum_i v_i c_ij, c = V^dag r.
+// R, X: k FP64 even fields (element s of field j at base + j*fstride + s).
+// rnorm[j] = |r_j| (host values) for the operand scaling.
+hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, const double *rnorm)
+{
+    if (k < 1 || k > 32) return set_err(ctx, HISQ_ERR_INVALID_ARG, "tensor-core deflation: 1..32 right-hand sides");
+    if (n < 1 || n > 512) return set_err(ctx, HISQ_ERR_INVALID_ARG, "tensor-core deflation: 1..512 eigenpairs");
+    const int Vh = ctx->g.Vh;
+    const int L = 3 * Vh;
+    const size_t fstride = size_t(L); // double2 elements per even field
+    TRY_HISQ(tc_prepare_v(ctx, n));
+    TcState &S = tc_state(ctx);
+
+    // ---- projection operands: R' (2k columns), hi/lo
+    const int NP = 64;                        // 2k <= 64 columns, padded by zero fill
+    std::vector<float> sc(k);
+    for (int j = 0; j < k; j++) sc[j] = rnorm[j] > 0 ? float(std::sqrt(double(L)) / rnorm[j]) : 1.f;
+    const size_t rbytes = size_t(2) * k * L * 2 * sizeof(__half);
+    char *w = (char *)get_buf(ctx, BUF_TC_WORK, 2 * rbytes + 4096 + sizeof(float) * 8 * 64);
+    if (!w) return HISQ_ERR_OOM;
+    __half *rh = (__half *)w, *rl = (__half *)(w + rbytes);
+    float *dscale = (float *)(w + 2 * rbytes);
+    int *status = (int *)(w + 2 * rbytes + 2048);
+    HISQ_CUDA(cudaMemcpyAsync(dscale, sc.data(), sizeof(float) * k, cudaMemcpyHostToDevice, ctx->stream));
+    HISQ_CUDA(cudaMemsetAsync(status, 0, sizeof(int), ctx->stream));
+    ctx->launches++;
+    k_build_r<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(L, k, (const double2 *)R, fstride, dscale, rh, rl);
+    HISQ_CUDA(cudaGetLastError());
+
+    CUtensorMap mp[4];
+    const uint64_t Kp = uint64_t(2) * L;
+    if (!make_tmap(&mp[0], S.vm_hi, Kp, n, Kp * 2, 128) || !make_tmap(&mp[1], S.vm_lo, Kp, n, Kp * 2, 128) ||
+        !make_tmap(&mp[2], rh, Kp, 2 * k, Kp * 2, NP) || !make_tmap(&mp[3], rl, Kp, 2 * k, Kp * 2, NP))
+        return set_err(ctx, HISQ_ERR_CUDA, "tensor map encoding failed");
+    // split K over about two CTAs per SM
+    const int mtiles = (n + 127) / 128;
+    constexpr int MTP = 2; // 256 rows per CTA: hi + lo A tiles and B fit two 80 KB stages
+    const int mgroups = (mtiles + MTP - 1) / MTP;
+    int nsplit = std::max(1, ctx->num_sms / mgroups);
+    int kchunk = int(((Kp + nsplit - 1) / nsplit + TC_BK - 1) / TC_BK) * TC_BK;
+    nsplit = int((Kp + kchunk - 1) / kchunk);
+    const int Mrows = mgroups * MTP * 128;
+    float *part = (float *)get_buf(ctx, BUF_TC_PART, sizeof(float) * size_t(nsplit) * Mrows * NP);
+    double *C = (double *)get_buf(ctx, BUF_TC_C, sizeof(double) * size_t(n) * 2 * k);
+    if (!part || !C) return HISQ_ERR_OOM;
+    ExpandEpi none{};
+    TRY_HISQ((launch_gemm<MTP, NP, 2, 0>(ctx, dim3(nsplit, mgroups), mp, int(Kp), kchunk, Mrows, part, none, status)));
+    ctx->launches++;
+    k_reduce_part<<<(n * 2 * k + 255) / 256, 256, 0, ctx->stream>>>(nsplit, n, NP, 2 * k, part, C);
+    HISQ_CUDA(cudaGetLastError());
+
+    // ---- expansion operands on the host (n x k small): D' columns 4j..4j+3
+    std::vector<double> Ch(size_t(n) * 2 * k);
+    int hstatus = 0;
+    HISQ_CUDA(cudaMemcpyAsync(Ch.data(), C, sizeof(double) * Ch.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    HISQ_CUDA(cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (hstatus != 0) return set_err(ctx, HISQ_ERR_TIMEOUT, "tensor-core projection: pipeline wait timed out (%d)", hstatus);
+    const double shift = 4.0 * ctx->mass * ctx->mass;
+    const int NE = 4 * k;                     // columns of the expansion
+    const int NEP = ((NE + 15) / 16) * 16;
+    const int ldk = int(S.ld_sm);             // K extent of the expansion (2n padded)
+    std::vector<__half> dh(size_t(NEP) * ldk, __float2half(0.f)), dl(size_t(NEP) * ldk, __float2half(0.f));
+    std::vector<float> esc(4 * k);
+    const double sig = S.sigma;
+    for (int j = 0; j < k; j++) {
+        // c_ij = G_ij / (sigma_v * sc_j); d = c / lambda
+        double cmax = 0, dmax = 0;
+        std::vector<double> cr(n), ci(n), dr(n), di(n);
+        for (int i = 0; i < n; i++) {
+            const double g = 1.0 / (sig * sc[j]);
+            cr[i] = Ch[size_t(i) * 2 * k + 2 * j] * g;
+            ci[i] = Ch[size_t(i) * 2 * k + 2 * j + 1] * g;
+            const double lam = ctx->eig.eps[i] + shift;
+            dr[i] = cr[i] / lam;
+            di[i] = ci[i] / lam;
+            cmax = std::max(cmax, std::max(std::fabs(cr[i]), std::fabs(ci[i])));
+            dmax = std::max(dmax, std::max(std::fabs(dr[i]), std::fabs(di[i])));
+        }
+        const double tx = dmax > 0 ? 1.0 / dmax : 1.0, tr = cmax > 0 ? 1.0 / cmax : 1.0;
+        // GEMM column value = sigma_v * t * (sum v d) -> factor 1 / (sigma_v t)
+        esc[4 * j + 0] = esc[4 * j + 1] = float(1.0 / (sig * tx));
+        esc[4 * j + 2] = esc[4 * j + 3] = float(1.0 / (sig * tr));
+        auto put = [&](int col, int i, double a_re, double a_im) {
+            // K index (i, 0) multiplies Re v_i, (i, 1) multiplies Im v_i
+            const __half hr = __float2half_rn(float(a_re)), hi_ = __float2half_rn(float(a_im));
+            dh[size_t(col) * ldk + 2 * i] = hr;
+            dh[size_t(col) * ldk + 2 * i + 1] = hi_;
+            dl[size_t(col) * ldk + 2 * i] = __float2half_rn(float(a_re - double(__half2float(hr))));
+            dl[size_t(col) * ldk + 2 * i + 1] = __float2half_rn(float(a_im - double(__half2float(hi_))));
+        };
+        for (int i = 0; i < n; i++) {
+            const double xr = dr[i] * tx, xi = di[i] * tx, rr = cr[i] * tr, ri = ci[i] * tr;
+            // Re(v d) = Re v Re d - Im v Im d ; Im(v d) = Re v Im d + Im v Re d
+            put(4 * j + 0, i, xr, -xi);
+            put(4 * j + 1, i, xi, xr);
+            put(4 * j + 2, i, rr, -ri);
+            put(4 * j + 3, i, ri, rr);
+        }
+    }
+    const size_t dbytes = size_t(NEP) * ldk * sizeof(__half);
+    char *dbuf = (char *)get_buf(ctx, BUF_TC_D, 2 * dbytes + sizeof(float) * 4 * 64);
+    if (!dbuf) return HISQ_ERR_OOM;
+    __half *ddh = (__half *)dbuf, *ddl = (__half *)(dbuf + dbytes);
+    float *desc = (float *)(dbuf + 2 * dbytes);
+    HISQ_CUDA(cudaMemcpyAsync(ddh, dh.data(), dbytes, cudaMemcpyHostToDevice, ctx->stream));
+    HISQ_CUDA(cudaMemcpyAsync(ddl, dl.data(), dbytes, cudaMemcpyHostToDevice, ctx->stream));
+    HISQ_CUDA(cudaMemcpyAsync(desc, esc.data(), sizeof(float) * 4 * k, cudaMemcpyHostToDevice, ctx->stream));
+    // the TMA box of D' is as tall as the kernel's N (rows beyond NEP are zero filled)
+    const int NT = NEP <= 32 ? 32 : (NEP <= 64 ? 64 : 128);
+    CUtensorMap me[4];
+    if (!make_tmap(&me[0], S.sm_hi, ldk, L, S.ld_sm * 2, 128) || !make_tmap(&me[1], S.sm_lo, ldk, L, S.ld_sm * 2, 128) ||
+        !make_tmap(&me[2], ddh, ldk, NEP, size_t(ldk) * 2, NT) || !make_tmap(&me[3], ddl, ldk, NEP, size_t(ldk) * 2, NT))
+        return set_err(ctx, HISQ_ERR_CUDA, "tensor map encoding failed");
+    ExpandEpi epi{(double2 *)X, (double2 *)R, fstride, desc, k, L};
+    const int ntiles = (L + 127) / 128;
+    const int grid = std::min(ntiles, ctx->num_sms);
+    hisq_status st;
+    if (NT == 32) st = launch_gemm<1, 32, 4, 1>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
+    else if (NT == 64) st = launch_gemm<1, 64, 4, 1>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
+    else st = launch_gemm<1, 128, 3, 1>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
+    if (st != HISQ_OK) return st;
+    HISQ_CUDA(cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (hstatus != 0) return set_err(ctx, HISQ_ERR_TIMEOUT, "tensor-core expansion: pipeline wait timed out (%d)", hstatus);
+    return HISQ_OK;
+}
+
+} // namespace hisq
+
+using namespace hisq;
+
+// x_j = V Lambda^-1 V^dag b_j and r_j = b_j - V V^dag b_j for nrhs <= 32 host
+// fields, through the tensor-core batched deflation (test entry point).
+extern "C" hisq_status hisq_deflate_batch(hisq_ctx *ctx, int n, int nrhs, const double *b, double *x, double *r)
+{
+    if (!ctx) return HISQ_ERR_INVALID_ARG;
+    if (!b || !x || !r || nrhs < 1 || nrhs > 32) return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad batched deflation arguments");
+    if (ctx->eig.n <= 0) return set_err(ctx, HISQ_ERR_STATE, "no eigenpairs stored");
+    if (!(ctx->mass > 0)) return set_err(ctx, HISQ_ERR_STATE, "mass not set");
+    if (n <= 0 || n > ctx->eig.n) n = ctx->eig.n;
+    HISQ_CUDA(cudaSetDevice(ctx->device));
+    const int Vh = ctx->g.Vh;
+    const size_t full = size_t(ctx->g.V) * 48, s64 = spinor_bytes(64, Vh);
+    double *f = (double *)get_buf(ctx, BUF_ETA_FULL, full);
+    char *R = (char *)get_buf(ctx, BUF_B_RHI, s64 * nrhs);
+    char *X = (char *)get_buf(ctx, BUF_B_XHI, s64 * nrhs);
+    if (!f || !R || !X) return HISQ_ERR_OOM;
+    std::vector<double> norms(nrhs);
+    for (int j = 0; j < nrhs; j++) {
+        HISQ_CUDA(cudaMemcpyAsync(f, b + size_t(j) * ctx->g.V * 6, full, cudaMemcpyHostToDevice, ctx->stream));
+        TRY_HISQ(launch_gather_parity(ctx, f, 0, 64, R + s64 * j));
+        TRY_HISQ(launch_norm2(ctx, 64, R + s64 * j, 12));
+        double n2;
+        TRY_HISQ(read_slots(ctx, 12, 1, &n2));
+        norms[j] = std::sqrt(n2);
+    }
+    HISQ_CUDA(cudaMemsetAsync(X, 0, s64 * nrhs, ctx->stream));
+    TRY_HISQ(tc_deflate_batch(ctx, n, nrhs, (double *)R, (double *)X, norms.data()));
+    for (int j = 0; j < nrhs; j++) {
+        HISQ_CUDA(cudaMemsetAsync(f, 0, full, ctx->stream));
+        TRY_HISQ(launch_scatter_parity(ctx, X + s64 * j, 64, 0, f));
+        HISQ_CUDA(cudaMemcpyAsync(x + size_t(j) * ctx->g.V * 6, f, full, cudaMemcpyDeviceToHost, ctx->stream));
+        HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+        HISQ_CUDA(cudaMemsetAsync(f, 0, full, ctx->stream));
+        TRY_HISQ(launch_scatter_parity(ctx, R + s64 * j, 64, 0, f));
+        HISQ_CUDA(cudaMemcpyAsync(r + size_t(j) * ctx->g.V * 6, f, full, cudaMemcpyDeviceToHost, ctx->stream));
+        HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    return HISQ_OK;
+}

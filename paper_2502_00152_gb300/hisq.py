@@ -39,7 +39,8 @@ class HisqError(RuntimeError):
 class hisq_solve_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision_sloppy", ctypes.c_int),
                 ("link_precision_sloppy", ctypes.c_int), ("delta_rd", ctypes.c_double), ("deflate", ctypes.c_int),
-                ("n_defl", ctypes.c_int), ("delta_tr", ctypes.c_double), ("compute_full_residual", ctypes.c_int)]
+                ("n_defl", ctypes.c_int), ("delta_tr", ctypes.c_double), ("compute_full_residual", ctypes.c_int),
+                ("batch", ctypes.c_int)]
 
 
 class hisq_solve_stats(ctypes.Structure):
@@ -75,8 +76,8 @@ _PROTOS = [
     ("hisq_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("hisq_load_links", ctypes.c_int, [_CTX, _DP, _DP, ctypes.c_int, ctypes.c_double]),
     ("hisq_set_mass", ctypes.c_int, [_CTX, ctypes.c_double]),
-    ("hisq_apply_dslash", ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, _DP, _DP]),
-    ("hisq_apply_normal_op", ctypes.c_int, [_CTX, ctypes.c_int, _DP, _DP]),
+    ("hisq_apply_dslash", ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, ctypes.c_int, _DP, _DP]),
+    ("hisq_apply_normal_op", ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, _DP, _DP]),
     ("hisq_solve", ctypes.c_int, [_CTX, _DP, _DP, ctypes.c_int, ctypes.POINTER(hisq_solve_params),
                                   ctypes.POINTER(hisq_solve_stats)]),
     ("hisq_solve_device", ctypes.c_int, [_CTX, _VP, _VP, ctypes.c_int, ctypes.POINTER(hisq_solve_params),
@@ -206,17 +207,25 @@ def hisq_set_mass(ctx: Context, m: float) -> None:
     _check(ctx.handle, load_library().hisq_set_mass(ctx.handle, m))
 
 
-def hisq_apply_dslash(ctx: Context, out_parity: int, precision: int, field) -> np.ndarray:
+def _default_link_prec(precision: int, link_precision):
+    if link_precision is None:
+        return 64 if precision == 64 else 32
+    return link_precision
+
+
+def hisq_apply_dslash(ctx: Context, out_parity: int, precision: int, field, link_precision=None) -> np.ndarray:
     a = _field(field, ctx.V)
     out = np.zeros((ctx.V, 3), dtype=np.complex128)
-    _check(ctx.handle, load_library().hisq_apply_dslash(ctx.handle, out_parity, precision, _dp(a), _dp(out)))
+    lp = _default_link_prec(precision, link_precision)
+    _check(ctx.handle, load_library().hisq_apply_dslash(ctx.handle, out_parity, precision, lp, _dp(a), _dp(out)))
     return out
 
 
-def hisq_apply_normal_op(ctx: Context, precision: int, field) -> np.ndarray:
+def hisq_apply_normal_op(ctx: Context, precision: int, field, link_precision=None) -> np.ndarray:
     a = _field(field, ctx.V)
     out = np.zeros((ctx.V, 3), dtype=np.complex128)
-    _check(ctx.handle, load_library().hisq_apply_normal_op(ctx.handle, precision, _dp(a), _dp(out)))
+    lp = _default_link_prec(precision, link_precision)
+    _check(ctx.handle, load_library().hisq_apply_normal_op(ctx.handle, precision, lp, _dp(a), _dp(out)))
     return out
 
 
@@ -318,3 +327,18 @@ def hisq_deflate_noalloc(ctx: Context, b_dev, x_dev, n: int = 0) -> None:
             raise ValueError("fields must be contiguous CUDA tensors of 3*Vh complex128")
     _check(ctx.handle, load_library().hisq_deflate_noalloc(ctx.handle, n, ctypes.c_void_p(b_dev.data_ptr()),
                                                            ctypes.c_void_p(x_dev.data_ptr())))
+
+
+_PROTOS.append(("hisq_deflate_batch", ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, _DP, _DP, _DP]))
+
+
+def hisq_deflate_batch(ctx: Context, b, n: int = 0):
+    """Tensor-core batched deflation of host fields b (nrhs, V, 3): returns
+    (x, r) with x_j = V Lambda^-1 V^dag b_j and r_j = b_j - V V^dag b_j."""
+    b = np.asarray(b)
+    k = b.shape[0]
+    bb = _field(b, ctx.V, k)
+    x = np.zeros((k, ctx.V, 3), dtype=np.complex128)
+    r = np.zeros((k, ctx.V, 3), dtype=np.complex128)
+    _check(ctx.handle, load_library().hisq_deflate_batch(ctx.handle, n, k, _dp(bb), _dp(x), _dp(r)))
+    return x, r

@@ -12,6 +12,12 @@ from paper_2502_00152_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 TOL = {64: 1e-13, 32: 1e-6, 16: 5e-3}
+# (vector storage, link storage); FP16 anywhere means the FP16 tolerance
+COMBOS = [(64, 64), (32, 32), (16, 32), (32, 16), (16, 16)]
+
+
+def tol(vp, lp):
+    return TOL[min(vp, lp)]
 
 # lattices: the Naik-distinct minimum, L = 4 (x+3 == x-1 aliasing), ragged
 # half-volumes that do not fill a 256-thread block, and several tiles
@@ -26,9 +32,9 @@ def test_dslash_all_precisions(dims, antip):
         src = I.gaussian_field(dims, 17)
         for par in (0, 1):
             ref = dslash_ref(o, dims, src, par)
-            for prec in (64, 32, 16):
-                out = H.hisq_apply_dslash(ctx, par, prec, src)
-                assert rel(out, ref) <= TOL[prec], (par, prec, rel(out, ref))
+            for vp, lp in COMBOS:
+                out = H.hisq_apply_dslash(ctx, par, vp, src, link_precision=lp)
+                assert rel(out, ref) <= tol(vp, lp), (par, vp, lp, rel(out, ref))
                 # the other parity of the output is exactly zero
                 assert np.all(project_parity(dims, out, 1 - par) == 0)
     finally:
@@ -43,9 +49,8 @@ def test_dslash_long_recon12(dims):
         src = I.gaussian_field(dims, 18)
         for par in (0, 1):
             ref = dslash_ref(o, dims, src, par)
-            for prec in (32, 16):
-                assert rel(H.hisq_apply_dslash(ctx, par, prec, src), ref) <= TOL[prec]
-            assert rel(H.hisq_apply_dslash(ctx, par, 64, src), ref) <= TOL[64]
+            for vp, lp in COMBOS:
+                assert rel(H.hisq_apply_dslash(ctx, par, vp, src, link_precision=lp), ref) <= tol(vp, lp)
     finally:
         ctx.close()
 
@@ -75,16 +80,16 @@ def test_nonfinite_links_rejected():
         ctx.close()
 
 
-@pytest.mark.parametrize("prec", [64, 32, 16])
-def test_normal_operator(prec):
+@pytest.mark.parametrize("vp,lp", COMBOS)
+def test_normal_operator(vp, lp):
     dims = (6, 4, 6, 8)
     m = 0.02
     ctx, o = make(dims, mass=m)
     try:
         x = project_parity(dims, I.gaussian_field(dims, 19), 0)
         ref = o.apply_Aee(m, x)
-        out = H.hisq_apply_normal_op(ctx, prec, x)
-        assert rel(out, ref) <= TOL[prec] * (10 if prec == 16 else 1)
+        out = H.hisq_apply_normal_op(ctx, vp, x, link_precision=lp)
+        assert rel(out, ref) <= tol(vp, lp) * (10 if min(vp, lp) == 16 else 1)
     finally:
         ctx.close()
 
@@ -128,7 +133,7 @@ def test_dslash_full_size(cfg):
     try:
         src = I.gaussian_field(dims, 5)
         ref = dslash_ref(o, dims, src, 1)
-        for prec in (64, 32, 16):
-            assert rel(H.hisq_apply_dslash(ctx, 1, prec, src), ref) <= TOL[prec]
+        for vp, lp in COMBOS:
+            assert rel(H.hisq_apply_dslash(ctx, 1, vp, src, link_precision=lp), ref) <= tol(vp, lp)
     finally:
         ctx.close()

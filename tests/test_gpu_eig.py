@@ -72,14 +72,15 @@ def test_fp16_eigvecs_deflate(lat):
     assert rel(x, ref) <= 5e-3
 
 
-@pytest.mark.parametrize("vprec,sloppy", [(32, 32), (16, 16), (32, 64)])
-def test_deflated_solve_and_redeflation(lat, vprec, sloppy):
+@pytest.mark.parametrize("vprec,sloppy,lprec", [(32, 32, 32), (16, 16, 16), (32, 64, 64), (32, 16, 32)])
+def test_deflated_solve_and_redeflation(lat, vprec, sloppy, lprec):
     dims, m, ctx, o, w, vecs = lat
     n = 32
     H.hisq_set_eigvecs(ctx, vecs[:n], w[:n], vprec)
     eta = I.gaussian_source(dims, 8, 0)
-    plain, st0, s0 = H.hisq_solve(ctx, eta, H.hisq_default_solve_params(precision_sloppy=sloppy))
-    defl, st1, s1 = H.hisq_solve(ctx, eta, H.hisq_default_solve_params(precision_sloppy=sloppy, deflate=1))
+    kw = dict(precision_sloppy=sloppy, link_precision_sloppy=lprec)
+    plain, st0, s0 = H.hisq_solve(ctx, eta, H.hisq_default_solve_params(**kw))
+    defl, st1, s1 = H.hisq_solve(ctx, eta, H.hisq_default_solve_params(deflate=1, **kw))
     assert s0 == H.HISQ_OK and s1 == H.HISQ_OK
     assert o.full_residual(m, plain, eta) <= 1e-10
     assert o.full_residual(m, defl, eta) <= 1e-10

@@ -19,8 +19,8 @@ def _kappa_bound(m, lam_max=30.0):
     return lam_max / (4 * m * m)
 
 
-@pytest.mark.parametrize("prec", [64, 32, 16])
-def test_c1_solve_matches_oracle(prec):
+@pytest.mark.parametrize("prec,lprec", [(64, 64), (32, 32), (16, 32), (16, 16)])
+def test_c1_solve_matches_oracle(prec, lprec):
     """8^4, m = 0.05, point source: plain even-odd CG (FP64) and the
     mixed-precision variants with FP64 reliable updates."""
     c = I.lattice_config("c1")
@@ -28,7 +28,7 @@ def test_c1_solve_matches_oracle(prec):
     ctx, o = make(dims, seed=c["seed"], eps=c["eps"], mass=m)
     try:
         eta = I.point_source(dims, 0)
-        prm = H.hisq_default_solve_params(tol=tol, precision_sloppy=prec)
+        prm = H.hisq_default_solve_params(tol=tol, precision_sloppy=prec, link_precision_sloppy=lprec)
         psi, st, status = H.hisq_solve(ctx, eta, prm)
         assert status == H.HISQ_OK and st[0]["converged"] == 1
         res = o.full_residual(m, psi, eta)
@@ -73,9 +73,11 @@ def test_z2_wall_source_and_recon12():
     ctx, o = make(dims, seed=5, eps=0.3, mass=m, recon=12)
     try:
         eta = I.z2_wall_source(dims, 7, 3, 1)
-        psi, st, status = H.hisq_solve(ctx, eta, H.hisq_default_solve_params(precision_sloppy=16))
-        assert status == H.HISQ_OK
-        assert o.full_residual(m, psi, eta) <= 1e-10
+        for lp in (32, 16):
+            psi, st, status = H.hisq_solve(ctx, eta, H.hisq_default_solve_params(precision_sloppy=16,
+                                                                                link_precision_sloppy=lp))
+            assert status == H.HISQ_OK
+            assert o.full_residual(m, psi, eta) <= 1e-10
     finally:
         ctx.close()
 
@@ -130,9 +132,31 @@ def test_full_size_solve_true_residual():
     ctx, o = make(dims, seed=c["seed"], eps=c["eps"], mass=m)
     try:
         eta = I.gaussian_source(dims, 11, 0)
-        for prec in (32, 16):
-            psi, st, status = H.hisq_solve(ctx, eta, H.hisq_default_solve_params(precision_sloppy=prec))
+        for prec, lp in ((32, 32), (16, 32)):
+            psi, st, status = H.hisq_solve(ctx, eta, H.hisq_default_solve_params(precision_sloppy=prec,
+                                                                                 link_precision_sloppy=lp))
             assert status == H.HISQ_OK
             assert o.full_residual(m, psi, eta) <= 1e-10
+    finally:
+        ctx.close()
+
+
+def test_fp16_links_stagnation_is_reported():
+    """FP16 link storage perturbs the operator by ~5e-4 * lambda_max, more than
+    the smallest eigenvalue of the light-mass 32^3x64 workload; the solve must
+    then stop with HISQ_ERR_NOT_CONVERGED (stagnation), not run to max_iter."""
+    c = I.lattice_config("c2")
+    dims, m = c["dims"], c["mass"]
+    ctx, o = make(dims, seed=c["seed"], eps=c["eps"], mass=m)
+    try:
+        eta = I.gaussian_source(dims, 11, 0)
+        prm = H.hisq_default_solve_params(precision_sloppy=16, link_precision_sloppy=16, max_iter=20000)
+        psi, st, status = H.hisq_solve(ctx, eta, prm)
+        if status == H.HISQ_OK:
+            assert o.full_residual(m, psi, eta) <= 1e-10
+        else:
+            assert status == H.HISQ_ERR_NOT_CONVERGED
+            assert st[0]["iterations"] < 20000
+            assert "stagnation" in H.hisq_last_error(ctx)
     finally:
         ctx.close()
