@@ -334,13 +334,14 @@ __global__ void k_build_r(int L, int k, const double2 *__restrict__ R, size_t fs
     }
 }
 
-// C[i][col] = sum_split part[split][i][col] (fixed order), col < ncol
-__global__ void k_reduce_part(int nsplit, int n, int N, int ncol, const float *__restrict__ part, double *C)
+// C[i][col] = sum_split part[split][i][col] (fixed order), i < n, col < ncol;
+// each split holds Mrows rows of N columns
+__global__ void k_reduce_part(int nsplit, int n, int Mrows, int N, int ncol, const float *__restrict__ part, double *C)
 {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * ncol; t += gridDim.x * blockDim.x) {
         const int i = t / ncol, col = t % ncol;
         double s = 0;
-        for (int p = 0; p < nsplit; p++) s += part[(size_t(p) * n + i) * N + col];
+        for (int p = 0; p < nsplit; p++) s += part[(size_t(p) * Mrows + i) * N + col];
         C[t] = s;
     }
 }
@@ -478,7 +479,7 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
     ExpandEpi none{};
     TRY_HISQ((launch_gemm<MTP, NP, 2, 0>(ctx, dim3(nsplit, mgroups), mp, int(Kp), kchunk, Mrows, part, none, status)));
     ctx->launches++;
-    k_reduce_part<<<(n * 2 * k + 255) / 256, 256, 0, ctx->stream>>>(nsplit, n, NP, 2 * k, part, C);
+    k_reduce_part<<<(n * 2 * k + 255) / 256, 256, 0, ctx->stream>>>(nsplit, n, Mrows, NP, 2 * k, part, C);
     HISQ_CUDA(cudaGetLastError());
 
     // ---- expansion operands on the host (n x k small): D' columns 4j..4j+3
