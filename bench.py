@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=3, help="oracle CG iterations per CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rhs-per-step", type=int, default=None,
+                    help="right-hand sides solved together per step (batched); default 1, 24 for c3")
     return ap.parse_args()
 
 
@@ -214,8 +216,14 @@ def run_ours(a):
 
     # sources: resident in HBM before the timed region (FP64 full-lattice fields)
     keep_links = (fat, lng) if (rank == 0 and world == 1 and not a.no_cpu_baseline) else (None, None)
+    kps = a.rhs_per_step if a.rhs_per_step is not None else (24 if a.config == "c3" else 1)
     nsrc = a.warmup + a.steps
-    srcs = [I.gaussian_source(dims, SOURCE_SEED, rank * 1000 + k) for k in range(nsrc)]
+    if kps == 1:
+        srcs = [I.gaussian_source(dims, SOURCE_SEED, rank * 1000 + k) for k in range(nsrc)]
+    else:
+        # Z2 wall sources: 8 timeslices x 3 colours per 24 right-hand sides
+        srcs = [np.stack([I.z2_wall_source(dims, SOURCE_SEED + 97 * (rank * 1000 + k) + q // 24, (q % 24) // 3, q % 3)
+                          for q in range(kps)]) for k in range(nsrc)]
     eta_dev = [torch.from_numpy(s).to(f"cuda:{local}") for s in srcs]
     if keep_links[0] is None:
         del fat, lng
@@ -226,17 +234,25 @@ def run_ours(a):
                                             deflate=0, compute_full_residual=1)
 
     def solve(k, prm):
-        st, status = H.hisq_solve_device(ctx, eta_dev[k], psi_dev, 1, prm)
+        st, status = H.hisq_solve_device(ctx, eta_dev[k], psi_dev, kps, prm)
         if status != H.HISQ_OK:
             raise RuntimeError(f"solve did not converge: {st}")
-        return st[0]
+        if kps == 1:
+            return st[0]
+        agg = dict(st[0])
+        for key in ("iterations", "reliable_updates", "redeflations", "profiled_iterations"):
+            agg[key] = max(s[key] for s in st)
+        for key in ("seconds_dslash_oe", "seconds_dslash_eo"):
+            agg[key] = sum(s[key] for s in st)
+        agg["full_residual"] = max(s["full_residual"] for s in st)
+        return agg
 
     # plain mixed-precision CG on the same GPU (comparison, not the headline)
     torch.cuda.synchronize()
     t0 = time.time()
     plain = [solve(k % nsrc, prm_plain) for k in range(a.plain_steps)]
     torch.cuda.synchronize()
-    plain_ms = (time.time() - t0) * 1e3 / max(1, a.plain_steps)
+    plain_ms = (time.time() - t0) * 1e3 / max(1, a.plain_steps) / kps
 
     for k in range(a.warmup):
         solve(k, prm_defl)
@@ -257,20 +273,20 @@ def run_ours(a):
     launches = H.hisq_kernel_launches(ctx) - l0
     clk = clocks.stop()
     H.hisq_set_profiling(ctx, False)
-    elapsed_ms, value = replica_time(ev0.elapsed_time(ev1), a.steps, f"cuda:{local}")
+    elapsed_ms, value = replica_time(ev0.elapsed_time(ev1), a.steps * kps, f"cuda:{local}")
     if world > 1:
         torch.distributed.barrier()
-    ms_per_step = elapsed_ms / a.steps
+    ms_per_step = elapsed_ms / a.steps  # one step = kps right-hand sides
 
     # end to end through the host API: pinned host source -> psi on the host
-    pin_eta = torch.from_numpy(srcs[a.warmup]).pin_memory()
+    pin_eta = torch.from_numpy(np.ascontiguousarray(srcs[a.warmup])).pin_memory()
     pin_psi = torch.empty_like(pin_eta).pin_memory()
     e2e_ms = []
     for k in range(a.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, st_h, status = H.hisq_solve(ctx, pin_eta.numpy(), prm_defl)
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3 / kps)
         if status != H.HISQ_OK:
             raise RuntimeError("host-API solve did not converge")
 
@@ -306,7 +322,10 @@ def run_ours(a):
         "config": {
             "workload": f"HISQ {dims[0]}^3x{dims[3]}, m={m}, {n_ev} eigenpairs (FP{a.eig_prec}), deflated "
                         f"mixed-precision CG (FP{a.sloppy} vectors, FP{a.links} links recon {a.recon}, FP64 "
-                        f"reliable updates), 1 Gaussian RHS per step, tol {tol}",
+                        f"reliable updates), "
+                        + ("1 Gaussian RHS per step" if kps == 1 else f"{kps} Z2 wall RHS per step, batched")
+                        + f", tol {tol}",
+            "rhs_per_step": kps,
             "lattice": list(dims), "mass": m, "n_ev": n_ev, "sloppy_vectors": f"fp{a.sloppy}",
             "links": f"fp{a.links} recon {a.recon}", "l2": "inputs larger than L2 (links and eigenvectors are GBs)",
             "parallelism": f"replicas{world}",
@@ -321,7 +340,7 @@ def run_ours(a):
             "dslash_gflops": round(flops_site * Vh / t_oe / 1e9, 1) if t_oe > 0 else None,
         },
         "e2e": {"value": round(sorted(e2e_ms)[len(e2e_ms) // 2], 4), "unit": "ms/RHS",
-                "h2d_bytes_per_step": V * 48, "d2h_bytes_per_step": V * 48},
+                "h2d_bytes_per_step": V * 48 * kps, "d2h_bytes_per_step": V * 48 * kps},
         "gpu_launches": int(launches),
         "clocks": clk,
         "plain_cg_ms_per_rhs": round(plain_ms, 3),

@@ -21,7 +21,7 @@ hisq_status read_slots(hisq_ctx *ctx, int slot0, int n, double *out);
 hisq_status deflate_add(hisq_ctx *ctx, int n, const double *r, double *x);
 hisq_status launch_defl_expand2(hisq_ctx *ctx, int n, int vprec, const void *V, const double *c_dev,
                                 const double *eps_dev, double shift, double *x, double *r);
-hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, const double *rnorm);
+hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, const double *rnorm, const int *field);
 
 // the tensor-core batched deflation applies to FP32-stored eigenvectors, up to
 // 512 of them and 32 right-hand sides per call
@@ -152,7 +152,7 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
         if (tc_eligible(ctx, n_defl, k)) {
             for (int j0 = 0; j0 < k; j0 += 32) {
                 const int kb = std::min(32, k - j0);
-                TRY(tc_deflate_batch(ctx, n_defl, kb, rh(j0), xh(j0), &ynorm[j0]));
+                TRY(tc_deflate_batch(ctx, n_defl, kb, rh(j0), xh(j0), &ynorm[j0], nullptr));
             }
             for (int j = 0; j < k; j++) {
                 double r2;
@@ -243,6 +243,22 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
         HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
         checked = it;
         bool changed = false;
+        std::vector<int> redefl;
+        // sloppy state of right-hand side j after a reliable update or a re-deflation
+        auto finalize = [&](int j, bool restart) -> hisq_status {
+            TRY(launch_convert(ctx, rh(j), 64, rs(j), prec));
+            TRY(launch_zero(ctx, xs(j), xprec));
+            double pp = rt[j] * rt[j];
+            if (restart) {
+                TRY(launch_convert(ctx, rh(j), 64, pj(j), prec));
+            } else {
+                TRY(launch_norm2(ctx, prec, pj(j), BS_PP));
+                TRY(read_slots(ctx, BS_PP, 1, &pp));
+            }
+            TRY(set_rhs_scalars(ctx, j, rt[j] * rt[j], pp));
+            r_last[j] = rt[j];
+            return HISQ_OK;
+        };
         for (int j : upd) {
             // reliable update of right-hand side j (FP64 true residual)
             TRY(launch_axpy_d(ctx, 1.0, xs(j), xprec, xh(j)));
@@ -271,34 +287,49 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
                 changed = true;
                 continue;
             }
-            bool restart = rt[j] > 10.0 * rn_seen[j];
+            const bool restart = rt[j] > 10.0 * rn_seen[j];
             if (n_defl > 0 && P->delta_tr > 0 && rt[j] < P->delta_tr * r_defl[j]) {
-                auto d0 = std::chrono::steady_clock::now();
-                TRY(deflate_pair_b(ctx, n_defl, y(j), rh(j), xh(j), t_hi, BS_R));
-                TRY(read_slots(ctx, BS_R, 1, &r2));
-                defl_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - d0).count();
-                rt[j] = std::sqrt(r2);
+                redefl.push_back(j);
+                continue;
+            }
+            TRY(finalize(j, restart));
+        }
+        // re-deflations of this round, together on the tensor cores when possible
+        if (!redefl.empty()) {
+            auto d0 = std::chrono::steady_clock::now();
+            if (tc_eligible(ctx, n_defl, int(redefl.size()))) {
+                for (size_t q0 = 0; q0 < redefl.size(); q0 += 32) {
+                    const int kb = int(std::min<size_t>(32, redefl.size() - q0));
+                    std::vector<double> nr(kb);
+                    for (int q = 0; q < kb; q++) nr[q] = rt[redefl[q0 + q]];
+                    TRY(tc_deflate_batch(ctx, n_defl, kb, rh(0), xh(0), nr.data(), &redefl[q0]));
+                }
+                for (int j : redefl) {
+                    double r2;
+                    TRY(launch_norm2(ctx, 64, rh(j), BS_R));
+                    TRY(read_slots(ctx, BS_R, 1, &r2));
+                    rt[j] = std::sqrt(r2);
+                }
+            } else {
+                for (int j : redefl) {
+                    double r2;
+                    TRY(deflate_pair_b(ctx, n_defl, y(j), rh(j), xh(j), t_hi, BS_R));
+                    TRY(read_slots(ctx, BS_R, 1, &r2));
+                    rt[j] = std::sqrt(r2);
+                }
+            }
+            defl_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - d0).count();
+            for (int j : redefl) {
                 r_defl[j] = rt[j];
                 st[j].redeflations++;
-                restart = true;
                 if (rt[j] <= target[j]) {
                     st[j].converged = 1;
                     done[j] = 1;
                     changed = true;
                     continue;
                 }
+                TRY(finalize(j, true));
             }
-            TRY(launch_convert(ctx, rh(j), 64, rs(j), prec));
-            TRY(launch_zero(ctx, xs(j), xprec));
-            double pp = rt[j] * rt[j];
-            if (restart) {
-                TRY(launch_convert(ctx, rh(j), 64, pj(j), prec));
-            } else {
-                TRY(launch_norm2(ctx, prec, pj(j), BS_PP));
-                TRY(read_slots(ctx, BS_PP, 1, &pp));
-            }
-            TRY(set_rhs_scalars(ctx, j, rt[j] * rt[j], pp));
-            r_last[j] = rt[j];
         }
         if (changed) {
             act.clear();

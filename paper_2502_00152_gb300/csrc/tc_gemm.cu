@@ -86,6 +86,7 @@ struct ExpandEpi {
     double2 *r;
     size_t fstride;   // double2 elements between fields
     const float *scale; // 4 per right-hand side: x re/im, r re/im column factors
+    const int *field; // column group j -> field index
     int k;
     int rows;         // L = 3 Vh
 };
@@ -245,8 +246,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             const int j = (c0 + i) >> 2;
                             if (j < epi.k) {
                                 const float *sc = epi.scale + 4 * j;
-                                double2 *xp = epi.x + epi.fstride * j + s;
-                                double2 *rp = epi.r + epi.fstride * j + s;
+                                const size_t f = size_t(epi.field[j]);
+                                double2 *xp = epi.x + epi.fstride * f + s;
+                                double2 *rp = epi.r + epi.fstride * f + s;
                                 double2 xv = *xp, rv = *rp;
                                 xv.x += double(v[i + 0]) * sc[0];
                                 xv.y += double(v[i + 1]) * sc[1];
@@ -311,14 +313,14 @@ __global__ void k_build_v(int Vh, int n, const char *__restrict__ V32, size_t vs
 }
 
 // R' columns 2j = (Re r_j, Im r_j), 2j+1 = (Im r_j, -Re r_j), times scale[j], hi/lo
-__global__ void k_build_r(int L, int k, const double2 *__restrict__ R, size_t fstride, const float *scale, __half *rh,
-                          __half *rl)
+__global__ void k_build_r(int L, int k, const double2 *__restrict__ R, size_t fstride, const int *field,
+                          const float *scale, __half *rh, __half *rl)
 {
     const size_t total = size_t(L) * k;
     for (size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += size_t(gridDim.x) * blockDim.x) {
         const int j = int(t / L);
         const size_t s = t % L;
-        const double2 v = R[fstride * j + s];
+        const double2 v = R[fstride * size_t(field[j]) + s];
         const float a = float(v.x * scale[j]), b = float(v.y * scale[j]);
         const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
         const __half la = __float2half_rn(a - __half2float(ha)), lb = __float2half_rn(b - __half2float(hb));
@@ -433,8 +435,9 @@ static hisq_status launch_gemm(hisq_ctx *ctx, dim3 grid, const CUtensorMap *m, i
 // Batched deflation of k right-hand sides with the first n stored eigenpairs:
 // x_j += sum_i v_i c_ij / lambda_i, r_j -= sum_i v_i c_ij, c = V^dag r.
 // R, X: k FP64 even fields (element s of field j at base + j*fstride + s).
-// rnorm[j] = |r_j| (host values) for the operand scaling.
-hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, const double *rnorm)
+// rnorm[j] = |r_j| (host values) for the operand scaling.  `field` (host,
+// nullable) maps right-hand side j to field field[j] of R and X.
+hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, const double *rnorm, const int *field)
 {
     if (k < 1 || k > 32) return set_err(ctx, HISQ_ERR_INVALID_ARG, "tensor-core deflation: 1..32 right-hand sides");
     if (n < 1 || n > 512) return set_err(ctx, HISQ_ERR_INVALID_ARG, "tensor-core deflation: 1..512 eigenpairs");
@@ -453,11 +456,15 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
     if (!w) return HISQ_ERR_OOM;
     __half *rh = (__half *)w, *rl = (__half *)(w + rbytes);
     float *dscale = (float *)(w + 2 * rbytes);
+    int *dfield = (int *)(w + 2 * rbytes + 1024);
     int *status = (int *)(w + 2 * rbytes + 2048);
+    std::vector<int> fl(k);
+    for (int j = 0; j < k; j++) fl[j] = field ? field[j] : j;
     HISQ_CUDA(cudaMemcpyAsync(dscale, sc.data(), sizeof(float) * k, cudaMemcpyHostToDevice, ctx->stream));
+    HISQ_CUDA(cudaMemcpyAsync(dfield, fl.data(), sizeof(int) * k, cudaMemcpyHostToDevice, ctx->stream));
     HISQ_CUDA(cudaMemsetAsync(status, 0, sizeof(int), ctx->stream));
     ctx->launches++;
-    k_build_r<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(L, k, (const double2 *)R, fstride, dscale, rh, rl);
+    k_build_r<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(L, k, (const double2 *)R, fstride, dfield, dscale, rh, rl);
     HISQ_CUDA(cudaGetLastError());
 
     CUtensorMap mp[4];
@@ -545,7 +552,7 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
     if (!make_tmap(&me[0], S.sm_hi, ldk, L, S.ld_sm * 2, 128) || !make_tmap(&me[1], S.sm_lo, ldk, L, S.ld_sm * 2, 128) ||
         !make_tmap(&me[2], ddh, ldk, NEP, size_t(ldk) * 2, NT) || !make_tmap(&me[3], ddl, ldk, NEP, size_t(ldk) * 2, NT))
         return set_err(ctx, HISQ_ERR_CUDA, "tensor map encoding failed");
-    ExpandEpi epi{(double2 *)X, (double2 *)R, fstride, desc, k, L};
+    ExpandEpi epi{(double2 *)X, (double2 *)R, fstride, desc, dfield, k, L};
     const int ntiles = (L + 127) / 128;
     const int grid = std::min(ntiles, ctx->num_sms);
     hisq_status st;
@@ -589,7 +596,7 @@ extern "C" hisq_status hisq_deflate_batch(hisq_ctx *ctx, int n, int nrhs, const 
         norms[j] = std::sqrt(n2);
     }
     HISQ_CUDA(cudaMemsetAsync(X, 0, s64 * nrhs, ctx->stream));
-    TRY_HISQ(tc_deflate_batch(ctx, n, nrhs, (double *)R, (double *)X, norms.data()));
+    TRY_HISQ(tc_deflate_batch(ctx, n, nrhs, (double *)R, (double *)X, norms.data(), nullptr));
     for (int j = 0; j < nrhs; j++) {
         HISQ_CUDA(cudaMemsetAsync(f, 0, full, ctx->stream));
         TRY_HISQ(launch_scatter_parity(ctx, X + s64 * j, 64, 0, f));

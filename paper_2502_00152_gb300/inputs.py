@@ -216,6 +216,8 @@ def lattice_config(name: str) -> dict:
         "c3": dict(dims=(32, 32, 32, 64), seed=2, eps=0.3, mass=0.002, tol=1e-10, n_ev=512),
         # learned initial guess
         "c4": dict(dims=(24, 24, 24, 48), seed=3, eps=0.3, mass=0.003, tol=1e-10, n_ev=128),
+        # small lattice for profiler captures (a few GB on the device at most)
+        "s16": dict(dims=(16, 16, 16, 32), seed=6, eps=0.3, mass=0.01, tol=1e-10, n_ev=64),
         # largest single-GPU lattice
         "c5": dict(dims=(64, 64, 64, 96), seed=4, eps=0.25, mass=0.0008, tol=1e-10, n_ev=200),
     }

@@ -19,6 +19,8 @@ def main():
     ap.add_argument("--iters", type=int, default=4)
     ap.add_argument("--sloppy", type=int, default=16)
     ap.add_argument("--recon", type=int, default=18)
+    ap.add_argument("--tc", type=int, default=0, help="also run the tensor-core batched deflation with this many "
+                                                     "random eigenvectors (24 right-hand sides)")
     a = ap.parse_args()
     c = I.lattice_config(a.config)
     dims = c["dims"]
@@ -31,6 +33,22 @@ def main():
                                       compute_full_residual=0)
     _, st, status = H.hisq_solve(ctx, eta, prm)
     print(f"{a.config} {dims}: {st[0]['iterations']} iterations, status {status}")
+    if a.tc > 0:
+        import numpy as np
+
+        from paper_2502_00152_gb300.inputs import random_normal
+
+        V = I.volume(dims)
+        par = (np.indices(dims[::-1]).sum(axis=0) & 1).reshape(-1)
+        vecs = random_normal(5, 77, 0, 6 * V * a.tc).reshape(a.tc, V, 3, 2)
+        vecs = vecs[..., 0] + 1j * vecs[..., 1]
+        vecs[:, par == 1] = 0
+        vecs /= np.linalg.norm(vecs.reshape(a.tc, -1), axis=1)[:, None, None]
+        H.hisq_set_eigvecs(ctx, vecs, np.linspace(0.01, 0.1, a.tc), 32)
+        bs = np.stack([I.gaussian_field(dims, 40 + j) for j in range(24)])
+        for _ in range(2):
+            H.hisq_deflate_batch(ctx, bs)
+        print(f"tensor-core deflation: {a.tc} vectors x 24 right-hand sides done")
     ctx.close()
 
 
