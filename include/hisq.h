@@ -87,6 +87,9 @@ typedef struct {
                                 application per iteration reads the links once);
                                 needs precision_sloppy 32|16 and FP32 links.
                                 0: one right-hand side after the other            */
+    int guess;               /* 1: psi holds an initial guess on entry (its even
+                                sites); the solve starts from it, deflating its
+                                residual when deflation is on                      */
 } hisq_solve_params;
 
 /* Per right-hand-side results of a solve. */
@@ -242,6 +245,31 @@ hisq_status hisq_load_eigvecs(hisq_ctx *ctx, const char *path);
  * Events are recorded on the context's stream around the two Dslash kernels of
  * every iteration; the sums are returned in hisq_solve_stats. */
 hisq_status hisq_set_profiling(hisq_ctx *ctx, int on);
+
+/* ---- learned initial guess: gauge-covariant parallel-transport layers.
+ * The paper has no learned part; these entry points serve a small network that
+ * predicts the CG starting vector (CG still runs to the same true residual).
+ * Channel tensors are (C, V, 3) complex64 on the device, full lattice, site
+ * s = x + X*(y + Y*(z + Z*t)); weights are (Cout, Cin, 9) complex64 on the device,
+ * hop 0 = identity, hop 1 + 2*mu + d = one-hop fat-link transport forward (d = 0,
+ * from x + mu) or backward (d = 1, from x - mu) with the Dirac operator's phases
+ * and signs, so weights (0, 1, ..., 1) give the fat-link part of D.
+ * out_b(x) = sum_a sum_h w[b][a][h] (T_h in_a)(x); 1 <= Cin, Cout <= 16. */
+
+/* out = layer(in) (adjoint = 0; Cout channels) or layer^dag(in) (adjoint = 1;
+ * in has Cout channels, out Cin).  w_bf16 = 1 rounds the weights to BF16 (FP32
+ * accumulation).  Ordered on the context's stream. */
+hisq_status hisq_net_layer(hisq_ctx *ctx, int cin, int cout, const float *w_dev, int w_bf16, int adjoint,
+                           const float *in_dev, float *out_dev);
+
+/* gw[b][a][h] = sum_x sum_c gout_b(x)_c conj((T_h in_a)(x)_c): the gradient
+ * dL/dconj(w) of a real loss L, given gout = dL/dconj(out). */
+hisq_status hisq_net_wgrad(hisq_ctx *ctx, int cin, int cout, const float *in_dev, const float *gout_dev,
+                           float *gw_dev);
+
+/* One Adam step (Kingma & Ba 2015) on n real parameters; step counts from 1. */
+hisq_status hisq_net_adam(hisq_ctx *ctx, int n, float *w_dev, const float *g_dev, float *m1_dev, float *m2_dev,
+                          float lr, float beta1, float beta2, float eps, int step);
 
 /* Device bytes held by the context. */
 size_t hisq_device_bytes(const hisq_ctx *ctx);

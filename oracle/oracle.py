@@ -246,3 +246,73 @@ def deflation_guess(evecs: np.ndarray, evals: np.ndarray, b: np.ndarray) -> np.n
     c = Vm.conj() @ np.asarray(b, dtype=np.complex128).reshape(-1)
     return (Vm.T @ (c / np.asarray(evals))).reshape(b.shape)
 
+
+
+# ------------------------------------------------------------------------
+# Learned initial guess: gauge-covariant parallel-transport network (the paper
+# has none; the oracle states the network's definition plainly).
+#   out_b(x) = sum_a sum_h w[b, a, h] (T_h in_a)(x)
+#   T_0 = 1,  T_{mu,fwd} f(x) =  eta_mu(x) bc(x) F_mu(x) f(x + mu),
+#             T_{mu,bwd} f(x) = -eta_mu(x) bc(x - mu) F_mu(x - mu)^dag f(x - mu)
+# hop index h = 1 + 2 mu + d (d = 0 fwd, 1 bwd).  With all hop weights 1 and
+# identity weight 0 one layer is the one-hop (fat-link) part of D.
+def _coords(dims):
+    X, Y, Z, T = dims
+    t, z, y, x = np.meshgrid(np.arange(T), np.arange(Z), np.arange(Y), np.arange(X), indexing="ij")
+    return [a.reshape(-1) for a in (x, y, z, t)]
+
+
+def _shift(dims, f, mu, n):
+    X, Y, Z, T = dims
+    g = f.reshape((T, Z, Y, X) + f.shape[1:])
+    return np.roll(g, -n, axis=3 - mu).reshape(f.shape)
+
+
+def net_transports(dims, fat, field, t_antiperiodic=True):
+    """The 9 transported copies [T_h field] of one (V, 3) colour field."""
+    c = _coords(dims)
+    T = dims[3]
+    fat = np.asarray(fat).reshape(-1, 4, 3, 3)
+    out = [np.array(field, dtype=np.complex128)]
+    for mu in range(4):
+        e = np.ones(len(c[0]))
+        for nu in range(mu):
+            e = e * np.where(c[nu] % 2 == 1, -1.0, 1.0)
+        bcf = np.where((mu == 3) & t_antiperiodic & (c[3] == T - 1), -1.0, 1.0) if mu == 3 else np.ones_like(e)
+        bcb = np.where(t_antiperiodic & (c[3] == 0), -1.0, 1.0) if mu == 3 else np.ones_like(e)
+        U = fat[:, mu]
+        fwd = np.einsum("sij,sj->si", U, _shift(dims, field, mu, 1)) * (e * bcf)[:, None]
+        Ub = _shift(dims, U, mu, -1)  # F_mu(x - mu)
+        bwd = -np.einsum("sji,sj->si", np.conj(Ub), _shift(dims, field, mu, -1)) * (e * bcb)[:, None]
+        out += [fwd, bwd]
+    return out
+
+
+def net_layer(dims, fat, w, ins, t_antiperiodic=True):
+    """One layer: w (Cout, Cin, 9), ins (Cin, V, 3) -> (Cout, V, 3)."""
+    w = np.asarray(w)
+    tr = [net_transports(dims, fat, f, t_antiperiodic) for f in ins]
+    out = np.zeros((w.shape[0],) + np.asarray(ins).shape[1:], dtype=np.complex128)
+    for b in range(w.shape[0]):
+        for a in range(w.shape[1]):
+            for h in range(9):
+                out[b] += w[b, a, h] * tr[a][h]
+    return out
+
+
+def net_wgrad(dims, fat, ins, gouts, t_antiperiodic=True):
+    """G[b, a, h] = sum_x gout_b(x) . conj(T_h in_a(x)) (gradient of a real loss
+    with respect to conj(w), given gout = its gradient with respect to conj(out))."""
+    tr = [net_transports(dims, fat, f, t_antiperiodic) for f in ins]
+    G = np.zeros((len(gouts), len(ins), 9), dtype=np.complex128)
+    for b in range(len(gouts)):
+        for a in range(len(ins)):
+            for h in range(9):
+                G[b, a, h] = np.vdot(tr[a][h], gouts[b])
+    return G
+
+
+def net_forward(dims, fat, weights, x, t_antiperiodic=True):
+    for w in weights:
+        x = net_layer(dims, fat, w, x, t_antiperiodic)
+    return x

@@ -137,6 +137,7 @@ void hisq_default_solve_params(hisq_solve_params *p)
     p->delta_tr = 1e-3;
     p->compute_full_residual = 1;
     p->batch = 1;
+    p->guess = 0;
 }
 
 void hisq_default_eig_params(hisq_eig_params *p)

@@ -142,8 +142,16 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
             return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite source %d", j);
         target[j] = P->tol * std::fmin(ynorm[j], 2.0 * m * etanorm[j]);
         HISQ_CUDA(cudaMemsetAsync(xh(j), 0, s64, ctx->stream));
-        HISQ_CUDA(cudaMemcpyAsync(rh(j), y(j), s64, cudaMemcpyDeviceToDevice, ctx->stream));
-        rt[j] = ynorm[j];
+        if (P->guess) { // start from the caller's guess (even sites of psi_j)
+            TRY(launch_gather_parity(ctx, psi + full * j, 0, 64, xh(j)));
+            TRY(residual_hi_b(ctx, y(j), xh(j), rh(j), t_hi, BS_R));
+            double r2;
+            TRY(read_slots(ctx, BS_R, 1, &r2));
+            rt[j] = std::sqrt(r2);
+        } else {
+            HISQ_CUDA(cudaMemcpyAsync(rh(j), y(j), s64, cudaMemcpyDeviceToDevice, ctx->stream));
+            rt[j] = ynorm[j];
+        }
     }
     // deflated guesses of all right-hand sides: one tensor-core projection and
     // one expansion for the whole batch, else one pair of passes per RHS
@@ -152,7 +160,7 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
         if (tc_eligible(ctx, n_defl, k)) {
             for (int j0 = 0; j0 < k; j0 += 32) {
                 const int kb = std::min(32, k - j0);
-                TRY(tc_deflate_batch(ctx, n_defl, kb, rh(j0), xh(j0), &ynorm[j0], nullptr));
+                TRY(tc_deflate_batch(ctx, n_defl, kb, rh(j0), xh(j0), &rt[j0], nullptr));
             }
             for (int j = 0; j < k; j++) {
                 double r2;

@@ -509,6 +509,8 @@ enum BufId : int {
     BUF_TC_PART,       // projection partial tiles per K split
     BUF_TC_C,          // projected coefficients (FP64)
     BUF_TC_D,          // expansion operands
+    BUF_NET_PART,      // network weight-gradient partial sums
+    BUF_GUESS,         // even part of a caller's initial guess
     BUF_COUNT
 };
 

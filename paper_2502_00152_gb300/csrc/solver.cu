@@ -323,9 +323,16 @@ hisq_status solve_one(hisq_ctx *ctx, const hisq_solve_params *P, const double *e
         n_defl = P->n_defl > 0 ? std::min(P->n_defl, ctx->eig.n) : ctx->eig.n;
     }
     double defl_s = 0;
-    // x = 0, r = y; with deflation x = V Lambda^-1 V^dag y, r = y - V V^dag y
-    HISQ_CUDA(cudaMemcpyAsync(r_hi, y, spinor_bytes(64, Vh), cudaMemcpyDeviceToDevice, ctx->stream));
+    // x = 0 (or the caller's guess), r = y - A x; with deflation
+    // x += V Lambda^-1 V^dag r, r -= V V^dag r
     double r2 = nrm[0];
+    if (P->guess) {
+        TRY(launch_gather_parity(ctx, psi, 0, 64, x));
+        TRY(residual_hi(ctx, y, x, r_hi, t_hi, SL_RHI));
+        TRY(read_slots(ctx, SL_RHI, 1, &r2));
+    } else {
+        HISQ_CUDA(cudaMemcpyAsync(r_hi, y, spinor_bytes(64, Vh), cudaMemcpyDeviceToDevice, ctx->stream));
+    }
     if (n_defl > 0) {
         auto d0 = std::chrono::steady_clock::now();
         TRY(deflate_pair(ctx, n_defl, y, r_hi, x, t_hi, SL_RHI));
@@ -404,6 +411,9 @@ hisq_status hisq_solve(hisq_ctx *ctx, const double *eta, double *psi, int nrhs, 
             if (!de || !dp) return HISQ_ERR_OOM;
             auto t0 = std::chrono::steady_clock::now();
             HISQ_CUDA(cudaMemcpyAsync(de, eta + size_t(k0) * ctx->g.V * 6, bytes * kb, cudaMemcpyHostToDevice, ctx->stream));
+            if (params->guess)
+                HISQ_CUDA(cudaMemcpyAsync(dp, psi + size_t(k0) * ctx->g.V * 6, bytes * kb, cudaMemcpyHostToDevice,
+                                          ctx->stream));
             hisq_status s = solve_batched(ctx, params, de, dp, kb, stats ? stats + k0 : nullptr);
             if (s != HISQ_OK && s != HISQ_ERR_NOT_CONVERGED) return s;
             HISQ_CUDA(cudaMemcpyAsync(psi + size_t(k0) * ctx->g.V * 6, dp, bytes * kb, cudaMemcpyDeviceToHost, ctx->stream));
@@ -426,6 +436,8 @@ hisq_status hisq_solve(hisq_ctx *ctx, const double *eta, double *psi, int nrhs, 
         hisq_solve_stats st;
         auto t0 = std::chrono::steady_clock::now();
         HISQ_CUDA(cudaMemcpyAsync(de, eta + size_t(k) * ctx->g.V * 6, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        if (params->guess)
+            HISQ_CUDA(cudaMemcpyAsync(dp, psi + size_t(k) * ctx->g.V * 6, bytes, cudaMemcpyHostToDevice, ctx->stream));
         hisq_status s = solve_one(ctx, params, de, dp, &st);
         if (s != HISQ_OK && s != HISQ_ERR_NOT_CONVERGED) return s;
         HISQ_CUDA(cudaMemcpyAsync(psi + size_t(k) * ctx->g.V * 6, dp, bytes, cudaMemcpyDeviceToHost, ctx->stream));

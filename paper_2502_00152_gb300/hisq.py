@@ -40,7 +40,7 @@ class hisq_solve_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision_sloppy", ctypes.c_int),
                 ("link_precision_sloppy", ctypes.c_int), ("delta_rd", ctypes.c_double), ("deflate", ctypes.c_int),
                 ("n_defl", ctypes.c_int), ("delta_tr", ctypes.c_double), ("compute_full_residual", ctypes.c_int),
-                ("batch", ctypes.c_int)]
+                ("batch", ctypes.c_int), ("guess", ctypes.c_int)]
 
 
 class hisq_solve_stats(ctypes.Structure):
@@ -229,14 +229,17 @@ def hisq_apply_normal_op(ctx: Context, precision: int, field, link_precision=Non
     return out
 
 
-def hisq_solve(ctx: Context, eta, params: Optional[hisq_solve_params] = None):
-    """Solve M psi = eta for host field(s) eta ((V,3) or (nrhs,V,3)).
+def hisq_solve(ctx: Context, eta, params: Optional[hisq_solve_params] = None, guess=None):
+    """Solve M psi = eta for host field(s) eta ((V,3) or (nrhs,V,3)).  With
+    params.guess = 1, `guess` (same shape) is the initial guess.
     Returns (psi, [stats dicts], status)."""
     eta = np.asarray(eta)
     single = eta.ndim == 2
     nrhs = 1 if single else eta.shape[0]
     e = _field(eta, ctx.V, nrhs)
     psi = np.zeros((nrhs, ctx.V, 3), dtype=np.complex128)
+    if guess is not None:
+        psi[:] = np.asarray(guess, dtype=np.complex128).reshape(psi.shape)
     p = params or hisq_default_solve_params()
     stats = (hisq_solve_stats * max(nrhs, 1))()
     st = load_library().hisq_solve(ctx.handle, _dp(e), _dp(psi), nrhs, ctypes.byref(p), stats)
@@ -342,3 +345,37 @@ def hisq_deflate_batch(ctx: Context, b, n: int = 0):
     r = np.zeros((k, ctx.V, 3), dtype=np.complex128)
     _check(ctx.handle, load_library().hisq_deflate_batch(ctx.handle, n, k, _dp(bb), _dp(x), _dp(r)))
     return x, r
+
+
+_PROTOS += [
+    ("hisq_net_layer", ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP]),
+    ("hisq_net_wgrad", ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
+    ("hisq_net_adam", ctypes.c_int, [_CTX, ctypes.c_int, _VP, _VP, _VP, _VP, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_float, ctypes.c_float, ctypes.c_int]),
+]
+
+
+def _dev(t):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def hisq_net_layer(ctx: Context, w, inp, out, w_bf16: bool = False, adjoint: bool = False) -> None:
+    """Parallel-transport layer on torch complex64 CUDA tensors: w (Cout, Cin, 9),
+    inp (Cin or Cout, V, 3), out (Cout or Cin, V, 3)."""
+    cout, cin = int(w.shape[0]), int(w.shape[1])
+    _check(ctx.handle, load_library().hisq_net_layer(ctx.handle, cin, cout, _dev(w), 1 if w_bf16 else 0,
+                                                     1 if adjoint else 0, _dev(inp), _dev(out)))
+
+
+def hisq_net_wgrad(ctx: Context, inp, gout, gw) -> None:
+    cout, cin = int(gw.shape[0]), int(gw.shape[1])
+    _check(ctx.handle, load_library().hisq_net_wgrad(ctx.handle, cin, cout, _dev(inp), _dev(gout), _dev(gw)))
+
+
+def hisq_net_adam(ctx: Context, w, g, m1, m2, lr: float, step: int, beta1=0.9, beta2=0.999, eps=1e-8) -> None:
+    """Adam step in place on float32 views of the tensors (same shapes)."""
+    n = int(w.numel() * (2 if w.is_complex() else 1))
+    _check(ctx.handle, load_library().hisq_net_adam(ctx.handle, n, _dev(w), _dev(g), _dev(m1), _dev(m2), lr, beta1,
+                                                    beta2, eps, step))
