@@ -434,16 +434,6 @@ def run_reference(a):
     print(json.dumps(out), flush=True)
 
 
-if __name__ == "__main__":
-    args = parse()
-    if args.impl == "reference":
-        run_reference(args)
-    elif args.learned:
-        run_learned(args)
-    else:
-        run_ours(args)
-
-
 # ------------------------------------------------------------ learned guess
 def run_learned(a):
     """24^3 x 48, m = 0.003, 128 eigenpairs; the parallel-transport network is
@@ -540,3 +530,13 @@ def _even_rhs(H, ctx, eta, m, par_np):
     y = 2.0 * m * eta - d
     y[par_np == 1] = 0
     return y
+
+
+if __name__ == "__main__":
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    elif args.learned:
+        run_learned(args)
+    else:
+        run_ours(args)

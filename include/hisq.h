@@ -132,7 +132,11 @@ void hisq_default_eig_params(hisq_eig_params *p);
 
 /* Create a context on CUDA device `device` for an X*Y*Z*T lattice (each extent
  * even and >= 4).  `cuda_stream` is a cudaStream_t or NULL (the context creates
- * its own).  On success *out owns all device memory of the context. */
+ * a non-blocking stream of its own, which is NOT ordered with the legacy default
+ * stream).  The special handles cudaStreamLegacy and cudaStreamPerThread are
+ * accepted; pass cudaStreamLegacy to order the library's work with other work on
+ * the legacy default stream.  On success *out owns all device memory of the
+ * context. */
 hisq_status hisq_create(const int dims[4], int t_antiperiodic, int device, void *cuda_stream,
                         hisq_ctx **out);
 void hisq_destroy(hisq_ctx *ctx);

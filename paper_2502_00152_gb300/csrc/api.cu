@@ -22,6 +22,17 @@ int log_level()
     return lvl;
 }
 
+bool graphs_enabled(const hisq_ctx *ctx)
+{
+    static int on = -1;
+    if (on < 0) {
+        const char *e = getenv("HISQ_GRAPHS");
+        on = (e && atoi(e) == 0) ? 0 : 1;
+    }
+    const cudaStream_t s = ctx->stream;
+    return on && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+}
+
 hisq_status set_err(hisq_ctx *c, hisq_status s, const char *fmt, ...)
 {
     if (c) {

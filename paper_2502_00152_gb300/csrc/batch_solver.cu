@@ -215,14 +215,28 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
     const long long maxit = P->max_iter > 0 ? P->max_iter : 1;
     long long it = 0, checked = 0;
     std::vector<std::vector<int>> act_at(2); // active list of the iteration in each event slot
+    IterGraphs graphs;
+    int direct_ka = -1;
     while (!act.empty()) {
         const bool force = it >= maxit;
         if (!force) {
             const int ka = int(act.size());
-            TRY(launch_mrhs_dslash_tt(ctx, prec, lprec, PP, TT, ka));
-            TRY(launch_mrhs_dslash_update(ctx, prec, lprec, TT, PP, XS, RS, ka));
-            TRY(launch_mrhs_p_update(ctx, prec, RS, PP, ka));
-            HISQ_CUDA(cudaEventRecord(ev[it & 1], ctx->stream));
+            const int slot = int(it & 1);
+            auto iteration = [&](bool cap) -> hisq_status {
+                TRY(launch_mrhs_dslash_tt(ctx, prec, lprec, PP, TT, ka));
+                TRY(launch_mrhs_dslash_update(ctx, prec, lprec, TT, PP, XS, RS, ka));
+                TRY(launch_mrhs_p_update(ctx, prec, RS, PP, ka));
+                HISQ_CUDA(record_event(ctx, ev[slot], cap));
+                return HISQ_OK;
+            };
+            // the first iteration of each active-set size runs directly (lazy
+            // kernel set-up happens outside capture), later ones replay a graph
+            if (ka != direct_ka) {
+                TRY(iteration(false));
+                direct_ka = ka;
+            } else {
+                TRY(graph_run(ctx, graphs, slot, ka, iteration));
+            }
             act_at[it & 1] = act;
             for (int j : act) its[j]++;
             it++;

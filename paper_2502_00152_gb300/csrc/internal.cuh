@@ -128,13 +128,25 @@ __device__ __forceinline__ int dim_of(const Geom &g, int mu)
 }
 
 // checkerboard index of the site c + d * mu_hat (periodic wrap); |d| <= 3 < L
+// (selects instead of indexing by a loop variable keep c[] in registers)
+__device__ __forceinline__ int coord_of(const int c[4], int mu)
+{
+    return mu == 0 ? c[0] : (mu == 1 ? c[1] : (mu == 2 ? c[2] : c[3]));
+}
+
+__device__ __forceinline__ int stride_of(const Geom &g, int mu)
+{
+    return mu == 0 ? 1 : (mu == 1 ? g.X : (mu == 2 ? g.X * g.Y : g.X * g.Y * g.Z));
+}
+
 __device__ __forceinline__ int nb_cb(const Geom &g, const int c[4], int s, int mu, int d)
 {
     const int L = dim_of(g, mu);
-    int cn = c[mu] + d;
+    const int cm = coord_of(c, mu);
+    int cn = cm + d;
     cn += (cn < 0) ? L : 0;
     cn -= (cn >= L) ? L : 0;
-    return (s + (cn - c[mu]) * g.stride[mu]) >> 1;
+    return (s + (cn - cm) * stride_of(g, mu)) >> 1;
 }
 
 __device__ __forceinline__ int full_site(const Geom &g, const int c[4])
@@ -599,6 +611,73 @@ inline int grid_for(const hisq_ctx *ctx, long n, int threads, int blocks_per_sm)
     if (want > cap) want = cap;
     if (want < 1) want = 1;
     return int(want);
+}
+
+// ------------------------------------------------------- CUDA graph replay
+// The launches of one CG iteration are the same every iteration (all scalars
+// live in device memory), so they are captured once into a CUDA graph and
+// replayed: one cudaGraphLaunch instead of three kernel launches.  Up to four
+// variants (slot = iteration mod 4) carry the per-iteration event records.
+// Graphs are used only on a stream that can be captured (not the legacy or
+// per-thread default stream) and can be switched off with HISQ_GRAPHS=0.
+struct IterGraphs {
+    cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};
+    unsigned long long launches[4] = {0, 0, 0, 0};
+    long long key = -1;
+    void release()
+    {
+        for (int i = 0; i < 4; i++) {
+            if (exec[i]) cudaGraphExecDestroy(exec[i]);
+            exec[i] = nullptr;
+        }
+    }
+    ~IterGraphs() { release(); }
+};
+
+bool graphs_enabled(const hisq_ctx *ctx);
+
+// records `ev` on the context's stream, as a graph node while capturing
+inline cudaError_t record_event(hisq_ctx *ctx, cudaEvent_t ev, bool capturing)
+{
+    return capturing ? cudaEventRecordWithFlags(ev, ctx->stream, cudaEventRecordExternal)
+                     : cudaEventRecord(ev, ctx->stream);
+}
+
+// Enqueue `body(capturing)` through graph slot `slot`: captured on first use for
+// the current `key`, replayed afterwards; run directly when graphs are off.
+template <class F>
+hisq_status graph_run(hisq_ctx *ctx, IterGraphs &G, int slot, long long key, F &&body)
+{
+    if (!graphs_enabled(ctx)) return body(false);
+    if (key != G.key) {
+        G.release();
+        G.key = key;
+    }
+    if (!G.exec[slot]) {
+        const unsigned long long l0 = ctx->launches;
+        cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "graph capture begin");
+        hisq_status s = body(true);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(ctx->stream, &g);
+        if (s != HISQ_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return cuda_err(ctx, e, "graph capture end");
+        e = cudaGraphInstantiate(&G.exec[slot], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            G.exec[slot] = nullptr;
+            return cuda_err(ctx, e, "graph instantiate");
+        }
+        G.launches[slot] = ctx->launches - l0;
+        ctx->launches = l0; // counted when replayed
+    }
+    ctx->launches += G.launches[slot];
+    cudaError_t e = cudaGraphLaunch(G.exec[slot], ctx->stream);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "graph launch");
+    return HISQ_OK;
 }
 
 inline RedArgs red_args(hisq_ctx *ctx, int op, int slot0 = 0)

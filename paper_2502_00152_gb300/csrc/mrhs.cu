@@ -3,17 +3,17 @@
 //
 // A batch is k ordinary one-parity colour fields at a fixed byte stride; a list
 // of active slots (idx[q] = right-hand side of slot q) masks converged ones.
-// Work item t = site * groups + group: the `groups` lanes of one site are
-// adjacent in a warp, so their link loads hit the same addresses and each link
-// is read from memory once for all right-hand sides.  Each thread accumulates
-// kMrhsChunk right-hand sides.  Per-RHS reductions are deterministic: lanes of
-// equal group are combined by shuffles, warps in a fixed order, blocks by the
-// last block in block order.
+// Each thread computes one site for R right-hand sides, so every link it loads
+// serves R matrix-vector products from registers; the lanes of a warp take 32
+// consecutive sites of the same fields, so neighbour gathers are coalesced.
+// Per-RHS reductions are deterministic: lanes by a fixed shuffle tree, warps in
+// a fixed order, blocks by the last block in block order.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace hisq {
 
-constexpr int kMrhsChunk = 4;
 
 template <class S>
 struct BatchF {
@@ -45,30 +45,42 @@ static BatchF<S> batchf(void *base, int Vh, int prec)
     return BatchF<S>{(char *)base, spinor_bytes(prec, Vh), Vh};
 }
 
-// per-slot reduction of kMrhsChunk values per thread into partials[block][slot]
-// and, in the last block, the batch finish operation
-__device__ __forceinline__ void batch_reduce(const double (&v)[kMrhsChunk], int groups, int kact, const BatchRed &br)
+// Thread tiling of the batched kernels: a block holds nsg site groups of 32
+// consecutive sites; within a site group, warp c handles right-hand-side slots
+// c*R .. c*R+R-1 (nch = ceil(kact / R) warps per site group).  The lanes of a
+// warp therefore read one colour field at 32 consecutive sites (coalesced), and
+// the nch warps of a site group read the same links at about the same time, so
+// the links come from DRAM once per launch.
+struct MrhsTile {
+    int nch, nsg;
+    __device__ __forceinline__ int chunk() const { return (threadIdx.x >> 5) % nch; }
+    __device__ __forceinline__ int group() const { return (threadIdx.x >> 5) / nch; }
+};
+
+// per-slot sums of R values per thread into partials[block][slot] (lanes by a
+// fixed shuffle tree, site groups in order) and, in the last block, the sums
+// over blocks in block order followed by the batch finish operation
+template <int R>
+__device__ __forceinline__ void batch_reduce(double (&v)[R], const MrhsTile &tl, int kact, const BatchRed &br)
 {
-    __shared__ double sh[8][kMaxBatch];
+    __shared__ double sh[8][kMaxBatch]; // [site group][slot]
     __shared__ bool am_last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    double x[kMrhsChunk];
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int u = 0; u < kMrhsChunk; u++) {
-        x[u] = v[u];
-        for (int o = 16; o >= groups; o >>= 1) x[u] += __shfl_down_sync(0xffffffffu, x[u], o);
-    }
-    if (lane < groups) {
+    for (int u = 0; u < R; u++)
 #pragma unroll
-        for (int u = 0; u < kMrhsChunk; u++) {
-            const int q = lane * kMrhsChunk + u;
-            if (q < kMaxBatch) sh[warp][q] = x[u];
+        for (int o = 16; o >= 1; o >>= 1) v[u] += __shfl_down_sync(0xffffffffu, v[u], o);
+    if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < R; u++) {
+            const int q = tl.chunk() * R + u;
+            if (q < kMaxBatch) sh[tl.group()][q] = v[u];
         }
     }
     __syncthreads();
     for (int q = threadIdx.x; q < kact; q += blockDim.x) {
         double s = 0;
-        for (int w = 0; w < nwarps; w++) s += sh[w][q];
+        for (int w = 0; w < tl.nsg; w++) s += sh[w][q];
         br.partials[size_t(blockIdx.x) * kMaxBatch + q] = s;
     }
     __threadfence();
@@ -153,43 +165,46 @@ struct BEpiCG {
 };
 
 // ------------------------------------------------------------- the kernel
-template <class S, class Lk, class L12T, bool R12, class Epi>
-__global__ void __launch_bounds__(256)
-    k_dslash_mrhs(Geom g, int par, Lk L, L12T L12, float c3, BatchF<S> in, const BatchScalars *scal, int groups,
+template <int R, class S, class Lk, class L12T, bool R12, class Epi>
+__global__ void __launch_bounds__(512, 1)
+    k_dslash_mrhs(Geom g, int par, Lk L, L12T L12, float c3, BatchF<S> in, const BatchScalars *scal, MrhsTile tl,
                   Epi epi, BatchRed br)
 {
-    typedef typename Lk::real R;
+    typedef typename Lk::real Rl;
     const int kact = scal->kact;
-    double red[kMrhsChunk];
+    // slots past kact (a partial last chunk) gather an active field again and
+    // skip only the epilogue, so every gather is unconditional and the
+    // compiler can issue them all ahead of the arithmetic
+    int jj[R];
+    bool on[R];
 #pragma unroll
-    for (int u = 0; u < kMrhsChunk; u++) red[u] = 0;
-    const long total = long(g.Vh) * groups;
-    for (long t = long(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += long(gridDim.x) * blockDim.x) {
-        const int cb = int(t / groups), gi = int(t % groups);
+    for (int u = 0; u < R; u++) {
+        const int q = tl.chunk() * R + u;
+        on[u] = q < kact; // uniform over the warp
+        jj[u] = scal->idx[on[u] ? q : kact - 1];
+    }
+    double red[R];
+#pragma unroll
+    for (int u = 0; u < R; u++) red[u] = 0;
+    const int step = gridDim.x * tl.nsg * 32;
+    for (int cb = (blockIdx.x * tl.nsg + tl.group()) * 32 + (threadIdx.x & 31); cb < g.Vh; cb += step) {
         int c[4];
         cb_coords(g, par, cb, c);
         const int s = full_site(g, c);
-        int jj[kMrhsChunk];
+        CVec<Rl> acc[R];
 #pragma unroll
-        for (int u = 0; u < kMrhsChunk; u++) {
-            const int q = gi * kMrhsChunk + u;
-            jj[u] = q < kact ? scal->idx[q] : -1;
-        }
-        CVec<R> acc[kMrhsChunk];
-#pragma unroll
-        for (int u = 0; u < kMrhsChunk; u++) acc[u].zero();
+        for (int u = 0; u < R; u++) acc[u].zero();
 #pragma unroll 1
         for (int mu = 0; mu < 4; mu++) {
             const int f1 = nb_cb(g, c, s, mu, +1), b1 = nb_cb(g, c, s, mu, -1);
             const int f3 = nb_cb(g, c, s, mu, +3), b3 = nb_cb(g, c, s, mu, -3);
-            CMat<R> f, b;
+            CMat<Rl> f, b;
             L.load(mu, 0, cb, f, b);
 #pragma unroll
-            for (int u = 0; u < kMrhsChunk; u++) {
-                if (jj[u] < 0) continue;
+            for (int u = 0; u < R; u++) {
                 const S v = in.at(jj[u]);
-                mv_acc(acc[u], f, cvt<R>(v.load(f1)));
-                mv_acc(acc[u], b, cvt<R>(v.load(b1)));
+                mv_acc(acc[u], f, cvt<Rl>(v.load(f1)));
+                mv_acc(acc[u], b, cvt<Rl>(v.load(b1)));
             }
             if constexpr (R12) {
                 CMat<float> f3m, b3m;
@@ -201,8 +216,7 @@ __global__ void __launch_bounds__(256)
                     if (c[3] < 3) sb = -sb;
                 }
 #pragma unroll
-                for (int u = 0; u < kMrhsChunk; u++) {
-                    if (jj[u] < 0) continue;
+                for (int u = 0; u < R; u++) {
                     const S v = in.at(jj[u]);
                     mv_acc_scaled(acc[u], sf, f3m, cvt<float>(v.load(f3)));
                     mv_acc_scaled(acc[u], sb, b3m, cvt<float>(v.load(b3)));
@@ -210,40 +224,43 @@ __global__ void __launch_bounds__(256)
             } else {
                 L.load(mu, 1, cb, f, b);
 #pragma unroll
-                for (int u = 0; u < kMrhsChunk; u++) {
-                    if (jj[u] < 0) continue;
+                for (int u = 0; u < R; u++) {
                     const S v = in.at(jj[u]);
-                    mv_acc(acc[u], f, cvt<R>(v.load(f3)));
-                    mv_acc(acc[u], b, cvt<R>(v.load(b3)));
+                    mv_acc(acc[u], f, cvt<Rl>(v.load(f3)));
+                    mv_acc(acc[u], b, cvt<Rl>(v.load(b3)));
                 }
             }
         }
 #pragma unroll
-        for (int u = 0; u < kMrhsChunk; u++)
-            if (jj[u] >= 0) epi(cb, jj[u], acc[u], red[u]);
+        for (int u = 0; u < R; u++)
+            if (on[u]) epi(cb, jj[u], acc[u], red[u]);
     }
-    batch_reduce(red, groups, kact, br);
+    batch_reduce<R>(red, tl, kact, br);
 }
 
 // p_j = r_j + beta_j p_j, |p_j|^2
-template <class S>
-__global__ void __launch_bounds__(256)
-    k_p_update_mrhs(int Vh, BatchF<S> r, BatchF<S> p, const BatchScalars *scal, int groups, BatchRed br)
+template <int R, class S>
+__global__ void __launch_bounds__(512, 1)
+    k_p_update_mrhs(int Vh, BatchF<S> r, BatchF<S> p, const BatchScalars *scal, MrhsTile tl, BatchRed br)
 {
-    typedef typename S::real R;
+    typedef typename S::real Rl;
     const int kact = scal->kact;
-    double red[kMrhsChunk];
+    int jj[R];
 #pragma unroll
-    for (int u = 0; u < kMrhsChunk; u++) red[u] = 0;
-    const long total = long(Vh) * groups;
-    for (long t = long(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += long(gridDim.x) * blockDim.x) {
-        const int cb = int(t / groups), gi = int(t % groups);
+    for (int u = 0; u < R; u++) {
+        const int q = tl.chunk() * R + u;
+        jj[u] = q < kact ? scal->idx[q] : -1;
+    }
+    double red[R];
 #pragma unroll
-        for (int u = 0; u < kMrhsChunk; u++) {
-            const int q = gi * kMrhsChunk + u;
-            if (q >= kact) continue;
-            const int j = scal->idx[q];
-            const R beta = R(scal->beta[j]);
+    for (int u = 0; u < R; u++) red[u] = 0;
+    const int step = gridDim.x * tl.nsg * 32;
+    for (int cb = (blockIdx.x * tl.nsg + tl.group()) * 32 + (threadIdx.x & 31); cb < Vh; cb += step) {
+#pragma unroll
+        for (int u = 0; u < R; u++) {
+            if (jj[u] < 0) continue;
+            const int j = jj[u];
+            const Rl beta = Rl(scal->beta[j]);
             const S rj = r.at(j), pj = p.at(j);
             auto rv = rj.load(cb);
             auto pv = pj.load(cb);
@@ -256,16 +273,38 @@ __global__ void __launch_bounds__(256)
             red[u] += double(pv.norm2());
         }
     }
-    batch_reduce(red, groups, kact, br);
+    batch_reduce<R>(red, tl, kact, br);
 }
 
 // ------------------------------------------------------------- launch glue
-static int groups_for(int kact)
+// right-hand sides per thread: four keeps the link matrices, four accumulators
+// and eight gathered neighbours in registers (128 per thread) with all gathers
+// of a hop issued together
+constexpr int kMrhsR = 4;
+
+static MrhsTile mrhs_tile(int kact, int R)
 {
-    int g = (kact + kMrhsChunk - 1) / kMrhsChunk;
-    int p = 1;
-    while (p < g) p <<= 1;
-    return p; // power of two <= kMaxBatch / kMrhsChunk
+    MrhsTile t;
+    t.nch = std::max(1, (kact + R - 1) / R); // <= 16 for kact <= kMaxBatch = 64
+    t.nsg = std::max(1, 8 / t.nch);          // blocks of 8 warps, up to 16 when nch > 8
+    return t;
+}
+
+// blocks per SM of `kern` at `threads` threads, cached per kernel and shape
+template <class K>
+static int mrhs_blocks_per_sm(K kern, int threads)
+{
+    static int cache[17] = {0};
+    const int slot = threads / 32 > 16 ? 16 : threads / 32;
+    if (cache[slot] == 0) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, 0) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            n = 1;
+        }
+        cache[slot] = n;
+    }
+    return cache[slot];
 }
 
 struct LinksFvB {
@@ -287,30 +326,33 @@ struct LinksFvB {
     }
 };
 
-template <class S, class Epi>
-static hisq_status run_mrhs(hisq_ctx *ctx, int par, int link_prec, const BatchF<S> &in, int kact, const Epi &epi,
-                            BatchRed br)
+template <int R, class S, class Epi>
+static hisq_status run_mrhs_r(hisq_ctx *ctx, int par, const BatchF<S> &in, int kact, const Epi &epi, BatchRed br)
 {
     const int Vh = ctx->g.Vh;
-    const int groups = groups_for(kact);
-    if (link_prec != 32) return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched operator: FP32 links only");
+    const MrhsTile tl = mrhs_tile(kact, R);
+    const int threads = 32 * tl.nch * tl.nsg;
     LinksFvB L{ctx->links_f[par], Vh, ctx->long_recon == 12 ? 1 : 2};
     auto launch = [&](auto kern, auto L12) -> hisq_status {
-        static int bps = -1;
-        if (bps < 0) {
-            int n = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 256, 0) != cudaSuccess || n < 1) n = 1;
-            bps = n;
-        }
-        const int grid = grid_for(ctx, long(Vh) * groups, 256, bps);
-        kern<<<grid, 256, 0, ctx->stream>>>(ctx->g, par, L, L12, float(ctx->long_scale), in, ctx->bscal, groups, epi, br);
+        const int grid = grid_for(ctx, long(Vh), 32 * tl.nsg, mrhs_blocks_per_sm(kern, threads));
+        kern<<<grid, threads, 0, ctx->stream>>>(ctx->g, par, L, L12, float(ctx->long_scale), in, ctx->bscal, tl, epi,
+                                               br);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_err(ctx, e, "batched dslash launch");
         return HISQ_OK;
     };
     if (ctx->long_recon == 12)
-        return launch(k_dslash_mrhs<S, LinksFvB, LinksF12, true, Epi>, LinksF12{ctx->links_f12[par], Vh});
-    return launch(k_dslash_mrhs<S, LinksFvB, LinksF12, false, Epi>, LinksF12{nullptr, Vh});
+        return launch(k_dslash_mrhs<R, S, LinksFvB, LinksF12, true, Epi>, LinksF12{ctx->links_f12[par], Vh});
+    return launch(k_dslash_mrhs<R, S, LinksFvB, LinksF12, false, Epi>, LinksF12{nullptr, Vh});
+}
+
+template <class S, class Epi>
+static hisq_status run_mrhs(hisq_ctx *ctx, int par, int link_prec, const BatchF<S> &in, int kact, const Epi &epi,
+                            BatchRed br)
+{
+    if (link_prec != 32) return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched operator: FP32 links only");
+    if (kact < 1 || kact > kMaxBatch) return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched operator: 1..64 right-hand sides");
+    return run_mrhs_r<kMrhsR>(ctx, par, in, kact, epi, br);
 }
 
 BatchRed batch_red(hisq_ctx *ctx, int op)
@@ -357,23 +399,27 @@ hisq_status launch_mrhs_dslash_update(hisq_ctx *ctx, int prec, int link_prec, vo
 }
 
 // (3) p_j = r_j + beta_j p_j, pp_j
-hisq_status launch_mrhs_p_update(hisq_ctx *ctx, int prec, void *r, void *p, int kact)
+template <int R, class S>
+static hisq_status run_p_update(hisq_ctx *ctx, void *r, void *p, int kact, int prec)
 {
     const int Vh = ctx->g.Vh;
-    const int groups = groups_for(kact);
-    BatchRed br = batch_red(ctx, BFIN_P);
-    auto go = [&](auto kern, auto R, auto P) -> hisq_status {
-        int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 256, 0) != cudaSuccess || n < 1) n = 1;
-        const int grid = grid_for(ctx, long(Vh) * groups, 256, n);
-        kern<<<grid, 256, 0, ctx->stream>>>(Vh, R, P, ctx->bscal, groups, br);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_err(ctx, e, "batched p update");
-        return HISQ_OK;
-    };
+    const MrhsTile tl = mrhs_tile(kact, R);
+    const int threads = 32 * tl.nch * tl.nsg;
+    auto kern = k_p_update_mrhs<R, S>;
+    const int grid = grid_for(ctx, long(Vh), 32 * tl.nsg, mrhs_blocks_per_sm(kern, threads));
+    kern<<<grid, threads, 0, ctx->stream>>>(Vh, batchf<S>(r, Vh, prec), batchf<S>(p, Vh, prec), ctx->bscal, tl,
+                                            batch_red(ctx, BFIN_P));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_err(ctx, e, "batched p update");
+    return HISQ_OK;
+}
+
+hisq_status launch_mrhs_p_update(hisq_ctx *ctx, int prec, void *r, void *p, int kact)
+{
+    if (kact < 1 || kact > kMaxBatch) return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched p update: 1..64 right-hand sides");
     switch (prec) {
-    case 32: return go(k_p_update_mrhs<SpinorF>, batchf<SpinorF>(r, Vh, 32), batchf<SpinorF>(p, Vh, 32));
-    case 16: return go(k_p_update_mrhs<SpinorH>, batchf<SpinorH>(r, Vh, 16), batchf<SpinorH>(p, Vh, 16));
+    case 32: return run_p_update<kMrhsR, SpinorF>(ctx, r, p, kact, 32);
+    case 16: return run_p_update<kMrhsR, SpinorH>(ctx, r, p, kact, 16);
     }
     return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched sloppy precision must be 32 or 16");
 }

@@ -165,6 +165,7 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
         }
     };
 
+    IterGraphs graphs;
     double r_last = rt, r_defl = rt;
     double r_best = rt, rn_last_seen = rt;
     int no_progress = 0; // reliable updates in a row without halving the best true residual
@@ -175,13 +176,23 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
     for (;;) {
         bool force = false;
         if (k < maxit) {
-            if (prof) HISQ_CUDA(cudaEventRecord(pe[k & 3][0], ctx->stream));
-            TRY(launch_cg_dslash_tt(ctx, prec, lprec, p, tmp));
-            if (prof) HISQ_CUDA(cudaEventRecord(pe[k & 3][1], ctx->stream));
-            TRY(launch_cg_dslash_update(ctx, prec, lprec, xprec, tmp, p, x_sl, r_sl));
-            if (prof) HISQ_CUDA(cudaEventRecord(pe[k & 3][2], ctx->stream));
-            TRY(launch_cg_p_update(ctx, prec, r_sl, p));
-            HISQ_CUDA(cudaEventRecord(ev[k & 1], ctx->stream));
+            const int slot = int(k & 3);
+            auto iteration = [&](bool cap) -> hisq_status {
+                if (prof) HISQ_CUDA(record_event(ctx, pe[slot][0], cap));
+                TRY(launch_cg_dslash_tt(ctx, prec, lprec, p, tmp));
+                if (prof) HISQ_CUDA(record_event(ctx, pe[slot][1], cap));
+                TRY(launch_cg_dslash_update(ctx, prec, lprec, xprec, tmp, p, x_sl, r_sl));
+                if (prof) HISQ_CUDA(record_event(ctx, pe[slot][2], cap));
+                TRY(launch_cg_p_update(ctx, prec, r_sl, p));
+                HISQ_CUDA(record_event(ctx, ev[slot & 1], cap));
+                return HISQ_OK;
+            };
+            // the first iterations run directly (lazy kernel set-up happens outside capture)
+            if (k < 4) {
+                TRY(iteration(false));
+            } else {
+                TRY(graph_run(ctx, graphs, slot, 0, iteration));
+            }
             k++;
         } else {
             force = true;

@@ -174,10 +174,20 @@ class Context:
         self.close()
 
 
+_CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
+
+
 def hisq_create(dims, t_antiperiodic: bool = True, device: int = 0, cuda_stream: Optional[int] = None) -> Context:
+    """cuda_stream: a cudaStream_t handle (e.g. torch.cuda.Stream().cuda_stream)
+    for the context's work, or None for a stream of the context's own.  Handle 0,
+    which is what torch reports for its default stream, means the legacy default
+    stream and is passed on as cudaStreamLegacy, so that the library's kernels are
+    ordered with torch's work on that stream."""
     lib = load_library()
     d = (ctypes.c_int * 4)(*[int(x) for x in dims])
     h = _CTX()
+    if cuda_stream is not None and int(cuda_stream) == 0:
+        cuda_stream = _CUDA_STREAM_LEGACY
     st = lib.hisq_create(d, 1 if t_antiperiodic else 0, device, cuda_stream, ctypes.byref(h))
     _check(None, st)
     return Context(h, dims)

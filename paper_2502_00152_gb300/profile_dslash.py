@@ -2,7 +2,7 @@
 capture the Dslash kernels in the same launch configuration as the solve.
 
 usage: python -m paper_2502_00152_gb300.profile_dslash [--config c4] [--iters 4]
-                                                      [--sloppy 16] [--recon 18]
+                                                      [--sloppy 16] [--recon 18] [--mrhs K]
 Kernel order of one call: source preparation and initial residual (three FP64
 Dslash launches), then per CG iteration the D_oe kernel, the fused D_eo + update
 kernel and the direction update.
@@ -21,6 +21,8 @@ def main():
     ap.add_argument("--recon", type=int, default=18)
     ap.add_argument("--tc", type=int, default=0, help="also run the tensor-core batched deflation with this many "
                                                      "random eigenvectors (24 right-hand sides)")
+    ap.add_argument("--mrhs", type=int, default=0, help="instead solve this many Gaussian right-hand sides together "
+                                                        "(batched operator) for --iters iterations")
     a = ap.parse_args()
     c = I.lattice_config(a.config)
     dims = c["dims"]
@@ -28,9 +30,14 @@ def main():
     ctx = H.hisq_create(dims, t_antiperiodic=True, device=0)
     H.hisq_load_links(ctx, fat, lng, long_recon=a.recon, long_scale=I.C3_NAIK if a.recon == 12 else 1.0)
     H.hisq_set_mass(ctx, c["mass"])
-    eta = I.gaussian_source(dims, 11, 0)
+    if a.mrhs > 1:
+        import numpy as np
+
+        eta = np.stack([I.gaussian_source(dims, 11, j) for j in range(a.mrhs)])
+    else:
+        eta = I.gaussian_source(dims, 11, 0)
     prm = H.hisq_default_solve_params(tol=1e-14, max_iter=a.iters, precision_sloppy=a.sloppy,
-                                      compute_full_residual=0)
+                                      compute_full_residual=0, batch=1 if a.mrhs > 1 else 0)
     _, st, status = H.hisq_solve(ctx, eta, prm)
     print(f"{a.config} {dims}: {st[0]['iterations']} iterations, status {status}")
     if a.tc > 0:

@@ -43,7 +43,7 @@ def test_layer_forward_adjoint_wgrad(cin, cout, bf16):
         H.hisq_net_layer(ctx, wd, xd, out, w_bf16=bf16)
         wq = w
         if bf16:  # the kernel rounds each weight to BF16
-            wq = torch.view_as_complex(torch.view_as_real(wd).to(torch.bfloat16).float()).numpy().astype(np.complex128)
+            wq = torch.view_as_complex(torch.view_as_real(wd).to(torch.bfloat16).float()).cpu().numpy().astype(np.complex128)
         ref = net_layer(dims, fat, wq.astype(np.complex64).astype(np.complex128), ins.astype(np.complex64).astype(np.complex128))
         assert rel(out.cpu().numpy(), ref) <= 2e-6
         # adjoint: <u, L v> = <L^dag u, v>
