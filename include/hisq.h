@@ -65,7 +65,8 @@ typedef enum {
 typedef enum {
     HISQ_PREC_DOUBLE = 64,
     HISQ_PREC_SINGLE = 32,
-    HISQ_PREC_HALF = 16 /* FP16 values with one FP32 scale per site (colour vectors) */
+    HISQ_PREC_HALF = 16, /* FP16 values with one FP32 scale per site (colour vectors) */
+    HISQ_PREC_BF16 = 15  /* BF16 values, 12 B per site; eigenvector storage only     */
 } hisq_precision;
 
 /* Parameters of a propagator solve (Sections 2 and 3). */
@@ -121,7 +122,7 @@ typedef struct {
                                 a_min > 0: given; a_min = -f < 0: placed where an
                                 estimated f * n_ev eigenvalues lie below it (0: f = 2) */
     double a_max;            /* > 0: given; <= 0: 1.1 x a power-iteration estimate  */
-    int storage_precision;   /* eigenvector storage: 32 or 16                        */
+    int storage_precision;   /* eigenvector storage: 32, 16 or HISQ_PREC_BF16 (15)    */
     uint64_t seed;           /* start vector                                        */
 } hisq_eig_params;
 
@@ -197,7 +198,7 @@ hisq_status hisq_get_eigvec(hisq_ctx *ctx, int i, double *out);
 
 /* Replace the stored eigenpairs by n host fields (even sites used; orthonormal)
  * with massless eigenvalues eps (nullable: recomputed as FP64 Rayleigh
- * quotients), stored at storage_precision 32 or 16. */
+ * quotients), stored at storage_precision 32, 16 or 15 (BF16). */
 hisq_status hisq_set_eigvecs(hisq_ctx *ctx, int n, const double *vecs, const double *eps,
                              int storage_precision);
 

@@ -21,14 +21,26 @@ hisq_status read_slots(hisq_ctx *ctx, int slot0, int n, double *out);
 hisq_status deflate_add(hisq_ctx *ctx, int n, const double *r, double *x);
 hisq_status launch_defl_expand2(hisq_ctx *ctx, int n, int vprec, const void *V, const double *c_dev,
                                 const double *eps_dev, double shift, double *x, double *r);
-hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, const double *rnorm, const int *field);
+hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, const double *rnorm, const int *field,
+                             bool update_r);
 
-// the tensor-core batched deflation applies to FP32-stored eigenvectors, up to
-// 512 of them and 32 right-hand sides per call
+// the tensor-core batched deflation applies to FP32- or BF16-stored
+// eigenvectors, up to 512 of them and 32 right-hand sides per call
 static bool tc_eligible(const hisq_ctx *ctx, int n, int k)
 {
-    return ctx->eig.prec == 32 && n >= 1 && n <= 512 && k >= 2;
+    return (ctx->eig.prec == 32 || ctx->eig.prec == HISQ_PREC_BF16) && n >= 1 && n <= 512 && k >= 2;
 }
+
+// r -= V c is the residual change of x += V Lambda^-1 c only while A v_i =
+// lambda_i v_i holds to well below the solve's tolerance.  A rounded vector
+// v = v_exact + dv has |A v - lambda v| ~ |A dv| <= lambda_max |dv|: about 5e-2
+// for BF16 (|dv| ~ 2e-3, lambda_max ~ 23), far above the low eigenvalues.  For
+// 16-bit storage the deflation increment dx is therefore formed on its own and
+// the residual updated by r -= A dx with the FP32 operator: dx lies in the low
+// modes, so the FP32 error of A dx, ~ 6e-8 |A| |dx| <= 6e-8 (lambda_max /
+// lambda_min) |r|, is of the size the FP32-vector update carries anyway, and
+// the next FP64 reliable update replaces r with b - A x.
+static bool dual_residual(const hisq_ctx *ctx) { return ctx->eig.prec == 32; }
 
 #define TRY(x)                                  \
     do {                                        \
@@ -104,12 +116,48 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
     double *t_hi = (double *)get_buf(ctx, BUF_TMPHI, s64);
     double *psi_o = (double *)get_buf(ctx, BUF_PSI_O, s64);
     if (!Y || !XH || !RH || !XS || !RS || !PP || !TT || !eta_e || !eta_o || !t_hi || !psi_o) return HISQ_ERR_OOM;
+    char *DX = nullptr, *F32 = nullptr;
+    const size_t s32 = spinor_bytes(32, Vh);
+    if (P->deflate && ctx->eig.n > 0 && !dual_residual(ctx)) {
+        DX = (char *)get_buf(ctx, BUF_B_DX, s64 * k);
+        F32 = (char *)get_buf(ctx, BUF_B_F32, s32 * 3);
+        if (!DX || !F32) return HISQ_ERR_OOM;
+    }
     auto y = [&](int j) { return (double *)(Y + s64 * j); };
     auto xh = [&](int j) { return (double *)(XH + s64 * j); };
     auto rh = [&](int j) { return (double *)(RH + s64 * j); };
     auto xs = [&](int j) { return (void *)(XS + sx * j); };
     auto rs = [&](int j) { return (void *)(RS + ssl * j); };
     auto pj = [&](int j) { return (void *)(PP + ssl * j); };
+    // tensor-core deflation of the right-hand sides `fields` (at most 32):
+    // x_j += V Lambda^-1 V^dag r_j and the matching r_j, |r_j| into rt[j]
+    auto tc_group = [&](const std::vector<int> &fields, int n_defl, std::vector<double> &rt) -> hisq_status {
+        std::vector<double> nr(fields.size());
+        for (size_t q = 0; q < fields.size(); q++) nr[q] = rt[fields[q]];
+        const int kb = int(fields.size());
+        if (dual_residual(ctx)) {
+            TRY(tc_deflate_batch(ctx, n_defl, kb, rh(0), xh(0), nr.data(), fields.data(), true));
+        } else {
+            auto dx = [&](int j) { return (double *)(DX + s64 * j); };
+            void *df = F32, *tf = F32 + s32, *af = F32 + 2 * s32;
+            for (int j : fields) HISQ_CUDA(cudaMemsetAsync(dx(j), 0, s64, ctx->stream));
+            TRY(tc_deflate_batch(ctx, n_defl, kb, rh(0), dx(0), nr.data(), fields.data(), false));
+            for (int j : fields) {
+                TRY(launch_convert(ctx, dx(j), 64, df, 32));
+                TRY(launch_dslash(ctx, 1, 32, 32, df, tf, 0, nullptr, 0, nullptr, 1.0, -1));  // D_oe dx
+                TRY(launch_dslash(ctx, 0, 32, 32, tf, af, m4, df, 0, nullptr, -1.0, -1));     // A dx
+                TRY(launch_axpy_d(ctx, -1.0, af, 32, rh(j)));
+                TRY(launch_axpy_d(ctx, 1.0, dx(j), 64, xh(j)));
+            }
+        }
+        for (int j : fields) {
+            double r2;
+            TRY(launch_norm2(ctx, 64, rh(j), BS_R));
+            TRY(read_slots(ctx, BS_R, 1, &r2));
+            rt[j] = std::sqrt(r2);
+        }
+        return HISQ_OK;
+    };
 
     int n_defl = 0;
     if (P->deflate) {
@@ -159,14 +207,9 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
         auto d0 = std::chrono::steady_clock::now();
         if (tc_eligible(ctx, n_defl, k)) {
             for (int j0 = 0; j0 < k; j0 += 32) {
-                const int kb = std::min(32, k - j0);
-                TRY(tc_deflate_batch(ctx, n_defl, kb, rh(j0), xh(j0), &rt[j0], nullptr));
-            }
-            for (int j = 0; j < k; j++) {
-                double r2;
-                TRY(launch_norm2(ctx, 64, rh(j), BS_R));
-                TRY(read_slots(ctx, BS_R, 1, &r2));
-                rt[j] = std::sqrt(r2);
+                std::vector<int> fields;
+                for (int j = j0; j < std::min(k, j0 + 32); j++) fields.push_back(j);
+                TRY(tc_group(fields, n_defl, rt));
             }
         } else {
             for (int j = 0; j < k; j++) {
@@ -214,19 +257,55 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
     } evfree{ev};
     const long long maxit = P->max_iter > 0 ? P->max_iter : 1;
     long long it = 0, checked = 0;
-    std::vector<std::vector<int>> act_at(2); // active list of the iteration in each event slot
+    std::vector<std::vector<int>> act_at(4); // active list of the iteration in each slot (it mod 4)
     IterGraphs graphs;
     int direct_ka = -1;
+    // optional kernel timing of the two batched Dslash launches: ring of 4
+    // iterations x 3 events; a launch's time is shared by its active right-hand sides
+    const bool prof = ctx->profile;
+    cudaEvent_t pe[4][3] = {};
+    struct ProfFree {
+        cudaEvent_t (*e)[3];
+        ~ProfFree()
+        {
+            for (int i = 0; i < 4; i++)
+                for (int q = 0; q < 3; q++)
+                    if (e[i][q]) cudaEventDestroy(e[i][q]);
+        }
+    } prof_free{pe};
+    if (prof)
+        for (int i = 0; i < 4; i++)
+            for (int q = 0; q < 3; q++) HISQ_CUDA(cudaEventCreate(&pe[i][q]));
+    long long retired = 0;
+    auto retire = [&](long long n_done) {
+        if (!prof) return;
+        for (; retired < n_done; retired++) {
+            float a = 0, b = 0;
+            cudaEvent_t *e = pe[retired & 3];
+            const std::vector<int> &on = act_at[retired & 3];
+            if (on.empty() || cudaEventElapsedTime(&a, e[0], e[1]) != cudaSuccess ||
+                cudaEventElapsedTime(&b, e[1], e[2]) != cudaSuccess)
+                continue;
+            for (int j : on) {
+                st[j].seconds_dslash_oe += a * 1e-3 / on.size();
+                st[j].seconds_dslash_eo += b * 1e-3 / on.size();
+                st[j].profiled_iterations++;
+            }
+        }
+    };
     while (!act.empty()) {
         const bool force = it >= maxit;
         if (!force) {
             const int ka = int(act.size());
-            const int slot = int(it & 1);
+            const int slot = int(it & 3);
             auto iteration = [&](bool cap) -> hisq_status {
+                if (prof) HISQ_CUDA(record_event(ctx, pe[slot][0], cap));
                 TRY(launch_mrhs_dslash_tt(ctx, prec, lprec, PP, TT, ka));
+                if (prof) HISQ_CUDA(record_event(ctx, pe[slot][1], cap));
                 TRY(launch_mrhs_dslash_update(ctx, prec, lprec, TT, PP, XS, RS, ka));
+                if (prof) HISQ_CUDA(record_event(ctx, pe[slot][2], cap));
                 TRY(launch_mrhs_p_update(ctx, prec, RS, PP, ka));
-                HISQ_CUDA(record_event(ctx, ev[slot], cap));
+                HISQ_CUDA(record_event(ctx, ev[slot & 1], cap));
                 return HISQ_OK;
             };
             // the first iteration of each active-set size runs directly (lazy
@@ -237,7 +316,7 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
             } else {
                 TRY(graph_run(ctx, graphs, slot, ka, iteration));
             }
-            act_at[it & 1] = act;
+            act_at[it & 3] = act;
             for (int j : act) its[j]++;
             it++;
         }
@@ -247,7 +326,8 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
             upd = act;
         } else if (jj >= checked) {
             HISQ_CUDA(cudaEventSynchronize(ev[jj & 1]));
-            for (int j : act_at[jj & 1]) {
+            retire(jj + 1);
+            for (int j : act_at[jj & 3]) {
                 const double rr = ctx->bmonitor_h[size_t(jj % ctx->bmonitor_len) * kMaxBatch + j];
                 if (!std::isfinite(rr)) {
                     cudaStreamSynchronize(ctx->stream);
@@ -263,6 +343,7 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
         }
         if (upd.empty()) continue;
         HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+        retire(it);
         checked = it;
         bool changed = false;
         std::vector<int> redefl;
@@ -321,16 +402,8 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
             auto d0 = std::chrono::steady_clock::now();
             if (tc_eligible(ctx, n_defl, int(redefl.size()))) {
                 for (size_t q0 = 0; q0 < redefl.size(); q0 += 32) {
-                    const int kb = int(std::min<size_t>(32, redefl.size() - q0));
-                    std::vector<double> nr(kb);
-                    for (int q = 0; q < kb; q++) nr[q] = rt[redefl[q0 + q]];
-                    TRY(tc_deflate_batch(ctx, n_defl, kb, rh(0), xh(0), nr.data(), &redefl[q0]));
-                }
-                for (int j : redefl) {
-                    double r2;
-                    TRY(launch_norm2(ctx, 64, rh(j), BS_R));
-                    TRY(read_slots(ctx, BS_R, 1, &r2));
-                    rt[j] = std::sqrt(r2);
+                    const size_t q1 = std::min(redefl.size(), q0 + 32);
+                    TRY(tc_group(std::vector<int>(redefl.begin() + q0, redefl.begin() + q1), n_defl, rt));
                 }
             } else {
                 for (int j : redefl) {
@@ -361,6 +434,7 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
         TRY(set_active(ctx, act));
     }
     HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    retire(it);
 
     // (a9) reconstruction and FP64 full residuals
     hisq_status worst = HISQ_OK;

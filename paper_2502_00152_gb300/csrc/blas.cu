@@ -30,8 +30,9 @@ static hisq_status with_spinor(hisq_ctx *ctx, int prec, const void *p, F &&f)
     case 64: return f(make_spinorD(q, Vh));
     case 32: return f(make_spinorF(q, Vh));
     case 16: return f(make_spinorH(q, Vh));
+    case HISQ_PREC_BF16: return f(make_spinorB(q, Vh));
     }
-    return set_err(ctx, HISQ_ERR_INVALID_ARG, "precision must be 64, 32 or 16");
+    return set_err(ctx, HISQ_ERR_INVALID_ARG, "precision must be 64, 32, 16 or 15 (BF16)");
 }
 
 // ------------------------------------------------------------- layout
@@ -170,10 +171,7 @@ hisq_status launch_cdot(hisq_ctx *ctx, int prec, const void *x, const void *y, i
 {
     return with_spinor(ctx, prec, x, [&](auto S) -> hisq_status {
         typedef decltype(S) ST;
-        ST Y = S;
-        if constexpr (sizeof(typename ST::real) == 8) Y = make_spinorD(const_cast<void *>(y), ctx->g.Vh);
-        else if constexpr (std::is_same<ST, SpinorF>::value) Y = make_spinorF(const_cast<void *>(y), ctx->g.Vh);
-        else Y = make_spinorH(const_cast<void *>(y), ctx->g.Vh);
+        const ST Y = make_like<ST>(const_cast<void *>(y), ctx->g.Vh);
         auto k = k_cdot<ST>;
         int grid = grid_for(ctx, ctx->g.Vh, 256, occ(k, 256));
         k<<<grid, 256, 0, ctx->stream>>>(ctx->g.Vh, S, Y, red_args(ctx, FIN_STORE, slot));
@@ -248,10 +246,7 @@ hisq_status launch_cg_p_update(hisq_ctx *ctx, int prec, const void *r, void *p)
 {
     return with_spinor(ctx, prec, p, [&](auto S) -> hisq_status {
         typedef decltype(S) ST;
-        ST R = S;
-        if constexpr (sizeof(typename ST::real) == 8) R = make_spinorD(const_cast<void *>(r), ctx->g.Vh);
-        else if constexpr (std::is_same<ST, SpinorF>::value) R = make_spinorF(const_cast<void *>(r), ctx->g.Vh);
-        else R = make_spinorH(const_cast<void *>(r), ctx->g.Vh);
+        const ST R = make_like<ST>(const_cast<void *>(r), ctx->g.Vh);
         auto k = k_p_update<ST>;
         int grid = grid_for(ctx, ctx->g.Vh, 256, occ(k, 256));
         k<<<grid, 256, 0, ctx->stream>>>(ctx->g.Vh, R, S, ctx->scal, red_args(ctx, FIN_CG_P));
@@ -274,6 +269,12 @@ __device__ __forceinline__ SpinorH spinor_at<SpinorH>(const char *base, size_t s
 {
     char *p = const_cast<char *>(base) + stride * i;
     return SpinorH{(uint4 *)p, Vh};
+}
+template <>
+__device__ __forceinline__ SpinorB spinor_at<SpinorB>(const char *base, size_t stride, int i, int Vh)
+{
+    char *p = const_cast<char *>(base) + stride * i;
+    return SpinorB{(__nv_bfloat162 *)p, Vh};
 }
 
 constexpr int kDeflVG = 8;        // vectors per block in the projection
@@ -364,13 +365,18 @@ hisq_status launch_defl_project(hisq_ctx *ctx, int n, int vprec, const void *V, 
     if (st != HISQ_OK) return st;
     dim3 grid((n + kDeflVG - 1) / kDeflVG, nchunks);
     const size_t stride = spinor_bytes(vprec, Vh);
-    if (vprec != 32 && vprec != 16) return set_err(ctx, HISQ_ERR_INVALID_ARG, "eigenvector precision must be 32 or 16");
+    if (vprec != 32 && vprec != 16 && vprec != HISQ_PREC_BF16)
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "eigenvector precision must be 32, 16 or 15 (BF16)");
     if (bprec != 64 && bprec != 32) return set_err(ctx, HISQ_ERR_INVALID_ARG, "projected vector must be FP64 or FP32");
     void *bb = const_cast<void *>(b);
     if (vprec == 32 && bprec == 64)
         k_defl_project<SpinorF, SpinorD><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, make_spinorD(bb, Vh), part, nchunks);
     else if (vprec == 32)
         k_defl_project<SpinorF, SpinorF><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, make_spinorF(bb, Vh), part, nchunks);
+    else if (vprec == HISQ_PREC_BF16 && bprec == 64)
+        k_defl_project<SpinorB, SpinorD><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, make_spinorD(bb, Vh), part, nchunks);
+    else if (vprec == HISQ_PREC_BF16)
+        k_defl_project<SpinorB, SpinorF><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, make_spinorF(bb, Vh), part, nchunks);
     else if (bprec == 64)
         k_defl_project<SpinorH, SpinorD><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, make_spinorD(bb, Vh), part, nchunks);
     else
@@ -437,6 +443,10 @@ hisq_status launch_defl_expand(hisq_ctx *ctx, int n, int vprec, const void *V, c
     if (vprec == 32 && xprec == 32) return expand_go<SpinorF>(ctx, n, V, stride, d_dev, coef, make_spinorF(x, Vh), smem);
     if (vprec == 16 && xprec == 64) return expand_go<SpinorH>(ctx, n, V, stride, d_dev, coef, make_spinorD(x, Vh), smem);
     if (vprec == 16 && xprec == 32) return expand_go<SpinorH>(ctx, n, V, stride, d_dev, coef, make_spinorF(x, Vh), smem);
+    if (vprec == HISQ_PREC_BF16 && xprec == 64)
+        return expand_go<SpinorB>(ctx, n, V, stride, d_dev, coef, make_spinorD(x, Vh), smem);
+    if (vprec == HISQ_PREC_BF16 && xprec == 32)
+        return expand_go<SpinorB>(ctx, n, V, stride, d_dev, coef, make_spinorF(x, Vh), smem);
     return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad deflation precisions");
 }
 
@@ -600,8 +610,10 @@ hisq_status launch_defl_project_ext(hisq_ctx *ctx, int n, int vprec, const void 
         k_defl_project<SpinorF, SpinorD><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, bs, part, nchunks);
     else if (vprec == 16)
         k_defl_project<SpinorH, SpinorD><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, bs, part, nchunks);
+    else if (vprec == HISQ_PREC_BF16)
+        k_defl_project<SpinorB, SpinorD><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, bs, part, nchunks);
     else
-        return set_err(ctx, HISQ_ERR_INVALID_ARG, "eigenvector precision must be 32 or 16");
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "eigenvector precision must be 32, 16 or 15 (BF16)");
     LAUNCH_CHECK("defl_project_ext");
     ctx->launches += 2;
     k_defl_finish<<<(n + 127) / 128, 128, 0, ctx->stream>>>(n, nchunks, part, (double2 *)c_dev, nullptr, 0.0);
@@ -676,6 +688,10 @@ hisq_status launch_defl_expand2(hisq_ctx *ctx, int n, int vprec, const void *V, 
         k<<<grid, 256, smem, ctx->stream>>>(Vh, n, (const char *)V, stride, (const double2 *)c_dev, eps_dev, shift, xs, rs);
     } else if (vprec == 16) {
         auto k = k_defl_expand2<SpinorH>;
+        int grid = grid_for(ctx, Vh, 256, occ(k, 256, smem));
+        k<<<grid, 256, smem, ctx->stream>>>(Vh, n, (const char *)V, stride, (const double2 *)c_dev, eps_dev, shift, xs, rs);
+    } else if (vprec == HISQ_PREC_BF16) {
+        auto k = k_defl_expand2<SpinorB>;
         int grid = grid_for(ctx, Vh, 256, occ(k, 256, smem));
         k<<<grid, 256, smem, ctx->stream>>>(Vh, n, (const char *)V, stride, (const double2 *)c_dev, eps_dev, shift, xs, rs);
     } else {

@@ -268,8 +268,8 @@ static hisq_status trlm(hisq_ctx *ctx, const hisq_eig_params *P, int *n_conv, do
     const int dim = 3 * Vh;
     if (n_ev < 1 || n_kr <= n_ev + 2 || n_keep < n_ev || n_keep >= n_kr || n_kr > dim || n_kr > 6144)
         return set_err(ctx, HISQ_ERR_INVALID_ARG, "need 1 <= n_ev <= n_keep < n_kr <= min(3 Vh, 6144), n_kr > n_ev + 2");
-    if (P->storage_precision != 32 && P->storage_precision != 16)
-        return set_err(ctx, HISQ_ERR_INVALID_ARG, "storage_precision must be 32 or 16");
+    if (P->storage_precision != 32 && P->storage_precision != 16 && P->storage_precision != HISQ_PREC_BF16)
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "storage_precision must be 32, 16 or 15 (BF16)");
     if (!(P->tol > 0)) return set_err(ctx, HISQ_ERR_INVALID_ARG, "tol must be positive");
 
     // basis (n_kr + 1 vectors), rotation output (n_keep), work
@@ -505,8 +505,8 @@ hisq_status hisq_set_eigvecs(hisq_ctx *ctx, int n, const double *vecs, const dou
 {
     if (!ctx) return HISQ_ERR_INVALID_ARG;
     if (n < 0 || (n > 0 && !vecs)) return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad eigenvector arguments");
-    if (storage_precision != 32 && storage_precision != 16)
-        return set_err(ctx, HISQ_ERR_INVALID_ARG, "storage_precision must be 32 or 16");
+    if (storage_precision != 32 && storage_precision != 16 && storage_precision != HISQ_PREC_BF16)
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "storage_precision must be 32, 16 or 15 (BF16)");
     if (!eps && !ctx->links_loaded) return set_err(ctx, HISQ_ERR_STATE, "links needed to recompute eigenvalues");
     HISQ_CUDA(cudaSetDevice(ctx->device));
     const int Vh = ctx->g.Vh;
@@ -591,7 +591,7 @@ hisq_status hisq_load_eigvecs(hisq_ctx *ctx, const char *path)
     bool ok = fread(&h, sizeof h, 1, fp) == 1 && memcmp(h.magic, "HISQEIG1", 8) == 0;
     const int Vh = ctx->g.Vh;
     ok = ok && h.dims[0] == ctx->g.X && h.dims[1] == ctx->g.Y && h.dims[2] == ctx->g.Z && h.dims[3] == ctx->g.T &&
-         (h.prec == 32 || h.prec == 16) && h.n > 0 && h.bytes_per_vec == int64_t(spinor_bytes(h.prec, Vh));
+         (h.prec == 32 || h.prec == 16 || h.prec == HISQ_PREC_BF16) && h.n > 0 && h.bytes_per_vec == int64_t(spinor_bytes(h.prec, Vh));
     if (!ok) {
         fclose(fp);
         return set_err(ctx, HISQ_ERR_INVALID_ARG, "%s: bad header or lattice mismatch", path);

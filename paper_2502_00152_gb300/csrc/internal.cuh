@@ -4,6 +4,7 @@
 // grid-wide reduction used by every norm and inner product.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -169,9 +170,11 @@ __device__ __forceinline__ float stag_phase(int mu, const int c[4])
 //  FP64: [3][Vh] double2                       48 B / site
 //  FP32: [Vh] float4 (colours 0,1) then [Vh] float2 (colour 2)   24 B / site
 //  FP16: [Vh] uint4 = 6 halves (re,im x 3) + FP32 scale          16 B / site
+//  BF16: [3][Vh] bf16x2 (re,im), eigenvector storage only         12 B / site
 inline size_t spinor_bytes(int prec, int Vh)
 {
-    return prec == 64 ? size_t(Vh) * 48 : (prec == 32 ? size_t(Vh) * 24 : size_t(Vh) * 16);
+    return prec == 64 ? size_t(Vh) * 48
+                      : (prec == 32 ? size_t(Vh) * 24 : (prec == HISQ_PREC_BF16 ? size_t(Vh) * 12 : size_t(Vh) * 16));
 }
 
 struct SpinorD {
@@ -263,6 +266,43 @@ struct SpinorH {
 inline SpinorD make_spinorD(void *p, int Vh) { return SpinorD{(double2 *)p, Vh}; }
 inline SpinorF make_spinorF(void *p, int Vh) { return SpinorF{(float4 *)p, (float2 *)((char *)p + size_t(Vh) * 16), Vh}; }
 inline SpinorH make_spinorH(void *p, int Vh) { return SpinorH{(uint4 *)p, Vh}; }
+
+// BF16 values, colour-major like FP64: the vector-major operand layout of the
+// tensor-core deflation GEMM (K index = (colour * Vh + cb) * 2 + re/im)
+struct SpinorB {
+    __nv_bfloat162 *p;
+    int Vh;
+    typedef float real;
+    __device__ __forceinline__ CVec<float> load(int i) const
+    {
+        CVec<float> v;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float2 f = __bfloat1622float2(p[size_t(c) * Vh + i]);
+            v.re[c] = f.x;
+            v.im[c] = f.y;
+        }
+        return v;
+    }
+    __device__ __forceinline__ void store(int i, const CVec<float> &v) const
+    {
+#pragma unroll
+        for (int c = 0; c < 3; c++) p[size_t(c) * Vh + i] = __floats2bfloat162_rn(v.re[c], v.im[c]);
+    }
+};
+inline SpinorB make_spinorB(void *p, int Vh) { return SpinorB{(__nv_bfloat162 *)p, Vh}; }
+
+// accessor of the same storage type as S for another field
+template <class S>
+inline S make_like(void *p, int Vh);
+template <>
+inline SpinorD make_like<SpinorD>(void *p, int Vh) { return make_spinorD(p, Vh); }
+template <>
+inline SpinorF make_like<SpinorF>(void *p, int Vh) { return make_spinorF(p, Vh); }
+template <>
+inline SpinorH make_like<SpinorH>(void *p, int Vh) { return make_spinorH(p, Vh); }
+template <>
+inline SpinorB make_like<SpinorB>(void *p, int Vh) { return make_spinorB(p, Vh); }
 
 // convert between accumulation types
 template <typename To, typename From>
@@ -517,6 +557,8 @@ enum BufId : int {
     BUF_B_RSL,
     BUF_B_P,
     BUF_B_TMP,
+    BUF_B_DX,          // batched solve: deflation increments (FP64, 16-bit eigenvectors)
+    BUF_B_F32,         // batched solve: three FP32 temporaries for A dx
     BUF_TC_WORK,       // tensor-core deflation: R' operands, scales, status
     BUF_TC_PART,       // projection partial tiles per K split
     BUF_TC_C,          // projected coefficients (FP64)
@@ -528,7 +570,7 @@ enum BufId : int {
 
 struct EigenStore {
     int n = 0;            // stored eigenpairs
-    int prec = 32;        // storage precision (32 or 16)
+    int prec = 32;        // storage precision (32, 16 or HISQ_PREC_BF16)
     void *vecs = nullptr; // n vectors of spinor_bytes(prec, Vh)
     std::vector<double> eps; // massless eigenvalues, ascending
     unsigned version = 0;    // bumped whenever the stored pairs change

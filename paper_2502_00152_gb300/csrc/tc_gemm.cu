@@ -9,11 +9,16 @@
 // the real product V R'^T gives (Re c_ij, Im c_ij) in columns (2j, 2j+1).  The
 // expansion uses the site-major copy of V, rows s, K = (i, re/im), against
 // D'_{4j..4j+3} built from d = c / lambda and c, so one GEMM updates x and r.
-// Every operand is split into an FP16 high part and an FP16 residual part and
-// three MMAs (hi*hi + hi*lo + lo*hi) are accumulated, which gives about 22
-// significant bits: enough for the updated residual to stay consistent with
-// the updated solution (r -= V c uses A v_i = lambda_i v_i).
+// FP32 eigenvectors: every operand is split into an FP16 high part and an FP16
+// residual part and three MMAs (hi*hi + hi*lo + lo*hi) are accumulated, which
+// gives about 22 significant bits: enough for the updated residual to stay
+// consistent with the updated solution (r -= V c uses A v_i = lambda_i v_i).
+// BF16 eigenvectors: the stored vectors are the A operand as they are (their
+// colour-major layout is the GEMM's K order); only the other operand is split
+// into BF16 high and low parts, two MMAs (a*hi + a*lo) per step, so the
+// products are those of the stored vectors to about 16 bits of the other side.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <cmath>
@@ -57,10 +62,10 @@ static PFN_encodeTiled_t encode_fn()
     return fn;
 }
 
-// 2D FP16 tensor: inner dimension `inner` elements (contiguous), `rows` rows of
+// 2D FP16 (or BF16) tensor: inner dimension `inner` elements (contiguous), `rows` rows of
 // `row_bytes`; box {64, box_rows}, 128-byte swizzle, zero fill out of bounds.
 static bool make_tmap(CUtensorMap *tm, const void *base, uint64_t inner, uint64_t rows, uint64_t row_bytes,
-                      uint32_t box_rows)
+                      uint32_t box_rows, bool bf16 = false)
 {
     PFN_encodeTiled_t enc = encode_fn();
     if (!enc) return false;
@@ -69,7 +74,7 @@ static bool make_tmap(CUtensorMap *tm, const void *base, uint64_t inner, uint64_
     cuuint64_t strides[1] = {row_bytes};
     cuuint32_t box[2] = {uint32_t(TC_BK), box_rows};
     cuuint32_t estr[2] = {1, 1};
-    return enc(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+    return enc(tm, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -83,7 +88,7 @@ static bool make_tmap(CUtensorMap *tm, const void *base, uint64_t inner, uint64_
 //            epilogue applies the result to the right-hand-side fields.
 struct ExpandEpi {
     double2 *x;       // k FP64 even fields, element s of field j at x + j*xs + s
-    double2 *r;
+    double2 *r;       // nullptr: x only (the caller recomputes r = b - A x)
     size_t fstride;   // double2 elements between fields
     const float *scale; // 4 per right-hand side: x re/im, r re/im column factors
     const int *field; // column group j -> field index
@@ -96,7 +101,7 @@ struct ExpandEpi {
 // only access TMEM lanes 32 * (w % 4) .. +31, so these four cover all 128 rows).
 constexpr int TC_THREADS = 192;
 
-template <int MT, int N, int STAGES, int MODE>
+template <int MT, int N, int STAGES, int MODE, bool BF16>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
               const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int K, int kchunk,
@@ -104,9 +109,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 {
     constexpr int A_TILE = 128 * TC_ROWB;               // 16 KB per 128-row tile
     constexpr int B_TILE = N * TC_ROWB;
-    constexpr int STAGE = 2 * MT * A_TILE + 2 * B_TILE; // hi + lo
+    constexpr int AP = BF16 ? 1 : 2;                      // A parts: hi (+ lo for FP16)
+    constexpr int STAGE = AP * MT * A_TILE + 2 * B_TILE;  // B: hi + lo
     constexpr int NCOLS = (MT * N <= 32) ? 32 : (MT * N <= 64) ? 64 : (MT * N <= 128) ? 128 : (MT * N <= 256) ? 256 : 512;
-    constexpr uint32_t IDESC = tc::idesc_f16_f32(128, N);
+    constexpr uint32_t IDESC = BF16 ? tc::idesc_bf16_f32(128, N) : tc::idesc_f16_f32(128, N);
     static_assert(N % 16 == 0 && N >= 16 && N <= 256, "N");
     static_assert(MT * N <= 512, "TMEM columns");
 
@@ -153,7 +159,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
         tc::prefetch_tmap(&tmAh);
-        tc::prefetch_tmap(&tmAl);
+        if (!BF16) tc::prefetch_tmap(&tmAl);
         tc::prefetch_tmap(&tmBh);
         tc::prefetch_tmap(&tmBl);
         uint32_t it = 0;
@@ -168,10 +174,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int kx = kbeg + kk * TC_BK;
                 for (int mt = 0; mt < MT; mt++) {
                     tc::tma_load_2d(st + mt * A_TILE, &tmAh, &full[s], kx, m0 + mt * 128);
-                    tc::tma_load_2d(st + (MT + mt) * A_TILE, &tmAl, &full[s], kx, m0 + mt * 128);
+                    if (!BF16) tc::tma_load_2d(st + (MT + mt) * A_TILE, &tmAl, &full[s], kx, m0 + mt * 128);
                 }
-                tc::tma_load_2d(st + 2 * MT * A_TILE, &tmBh, &full[s], kx, 0);
-                tc::tma_load_2d(st + 2 * MT * A_TILE + B_TILE, &tmBl, &full[s], kx, 0);
+                tc::tma_load_2d(st + AP * MT * A_TILE, &tmBh, &full[s], kx, 0);
+                tc::tma_load_2d(st + AP * MT * A_TILE + B_TILE, &tmBl, &full[s], kx, 0);
             }
         }
     producer_done:
@@ -192,18 +198,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (!tc::mbar_wait(&full[s], (it / STAGES) & 1, status, tc::TC_TIMEOUT_FULL)) goto mma_done;
                 tc::tc_fence_after();
                 const uint32_t st = tc::smem_addr(smem + s * STAGE);
-                const uint32_t bh = st + 2 * MT * A_TILE, bl = bh + B_TILE;
+                const uint32_t bh = st + AP * MT * A_TILE, bl = bh + B_TILE;
 #pragma unroll
                 for (int mt = 0; mt < MT; mt++) {
                     const uint32_t ah = st + mt * A_TILE, al = st + (MT + mt) * A_TILE;
 #pragma unroll
                     for (int q = 0; q < TC_BK / 16; q++) {
-                        const uint32_t off = q * 32; // 16 FP16 along K inside the swizzle atom
+                        const uint32_t off = q * 32; // 16 16-bit values along K inside the swizzle atom
                         const uint32_t d = taddr + mt * N;
                         const uint32_t acc0 = (kk > 0 || q > 0) ? 1u : 0u;
                         tc::mma_f16(d, tc::smem_desc_sw128(ah + off), tc::smem_desc_sw128(bh + off), IDESC, acc0);
                         tc::mma_f16(d, tc::smem_desc_sw128(ah + off), tc::smem_desc_sw128(bl + off), IDESC, 1u);
-                        tc::mma_f16(d, tc::smem_desc_sw128(al + off), tc::smem_desc_sw128(bh + off), IDESC, 1u);
+                        if (!BF16)
+                            tc::mma_f16(d, tc::smem_desc_sw128(al + off), tc::smem_desc_sw128(bh + off), IDESC, 1u);
                     }
                 }
                 tc::mma_commit(&empty[s]);
@@ -248,14 +255,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                 const float *sc = epi.scale + 4 * j;
                                 const size_t f = size_t(epi.field[j]);
                                 double2 *xp = epi.x + epi.fstride * f + s;
-                                double2 *rp = epi.r + epi.fstride * f + s;
-                                double2 xv = *xp, rv = *rp;
+                                double2 xv = *xp;
                                 xv.x += double(v[i + 0]) * sc[0];
                                 xv.y += double(v[i + 1]) * sc[1];
-                                rv.x -= double(v[i + 2]) * sc[2];
-                                rv.y -= double(v[i + 3]) * sc[3];
                                 *xp = xv;
-                                *rp = rv;
+                                if (epi.r) {
+                                    double2 *rp = epi.r + epi.fstride * f + s;
+                                    double2 rv = *rp;
+                                    rv.x -= double(v[i + 2]) * sc[2];
+                                    rv.y -= double(v[i + 3]) * sc[3];
+                                    *rp = rv;
+                                }
                             }
                         }
                     }
@@ -336,6 +346,51 @@ __global__ void k_build_r(int L, int k, const double2 *__restrict__ R, size_t fs
     }
 }
 
+// BF16 eigenvectors: site-major copy sm[s][i] (row pitch ld_sm bf16x2 pairs) of
+// the stored vector-major vectors V[i][s], s = colour * Vh + cb; 32 x 32 tiles
+// through shared memory so that both sides are coalesced.
+__global__ void k_build_v_sm_bf16(int L, int n, const __nv_bfloat162 *__restrict__ V, size_t vstride,
+                                  __nv_bfloat162 *__restrict__ sm, size_t ld_sm)
+{
+    __shared__ __nv_bfloat162 tile[32][33];
+    const int s0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int i = i0 + r, s = s0 + threadIdx.x;
+        if (i < n && s < L) tile[r][threadIdx.x] = V[vstride * i + s];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int s = s0 + r, i = i0 + threadIdx.x;
+        if (i < n && s < L) sm[ld_sm * s + i] = tile[threadIdx.x][r];
+    }
+}
+
+// R' for the BF16 GEMM: columns 2j = (Re r_j, Im r_j), 2j+1 = (Im r_j, -Re r_j),
+// times scale[j], split into BF16 high and low parts
+__global__ void k_build_r_bf16(int L, int k, const double2 *__restrict__ R, size_t fstride, const int *field,
+                               const float *scale, __nv_bfloat16 *rh, __nv_bfloat16 *rl)
+{
+    const size_t total = size_t(L) * k;
+    for (size_t t = size_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total; t += size_t(gridDim.x) * blockDim.x) {
+        const int j = int(t / L);
+        const size_t s = t % L;
+        const double2 v = R[fstride * size_t(field[j]) + s];
+        const float a = float(v.x * scale[j]), b = float(v.y * scale[j]);
+        const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+        const __nv_bfloat16 la = __float2bfloat16_rn(a - __bfloat162float(ha));
+        const __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
+        const size_t c0 = (size_t(2 * j) * L + s) * 2, c1 = (size_t(2 * j + 1) * L + s) * 2;
+        rh[c0] = ha;
+        rh[c0 + 1] = hb;
+        rl[c0] = la;
+        rl[c0 + 1] = lb;
+        rh[c1] = hb;
+        rh[c1 + 1] = __hneg(ha);
+        rl[c1] = lb;
+        rl[c1 + 1] = __hneg(la);
+    }
+}
+
 // C[i][col] = sum_split part[split][i][col] (fixed order), i < n, col < ncol;
 // each split holds Mrows rows of N columns
 __global__ void k_reduce_part(int nsplit, int n, int Mrows, int N, int ncol, const float *__restrict__ part, double *C)
@@ -352,8 +407,10 @@ __global__ void k_reduce_part(int nsplit, int n, int Mrows, int N, int ncol, con
 struct TcState {
     unsigned version = ~0u;     // eigenpair version the copies were built from
     int n = 0, Vh = 0;
-    __half *vm_hi = nullptr, *vm_lo = nullptr, *sm_hi = nullptr, *sm_lo = nullptr;
-    size_t ld_sm = 0;
+    bool bf16 = false;          // BF16 storage: vm_hi is the stored vectors, no lo parts
+    void *vm_hi = nullptr, *vm_lo = nullptr, *sm_hi = nullptr, *sm_lo = nullptr;
+    void *owned = nullptr;      // device copies owned by this state
+    size_t ld_sm = 0;           // 16-bit values per site-major row
     size_t bytes = 0;
     float sigma = 1;
 };
@@ -373,7 +430,7 @@ static TcState &tc_state(hisq_ctx *ctx)
 void tc_release(hisq_ctx *ctx)
 {
     TcState &S = tc_state(ctx);
-    if (S.vm_hi) dev_free(ctx, S.vm_hi, S.bytes);
+    if (S.owned) dev_free(ctx, S.owned, S.bytes);
     S = TcState{};
 }
 
@@ -388,15 +445,40 @@ static hisq_status tc_prepare_v(hisq_ctx *ctx, int n)
     TcState &S = tc_state(ctx);
     const int Vh = ctx->g.Vh;
     if (S.version == ctx->eig.version && S.n == n && S.Vh == Vh && S.vm_hi) return HISQ_OK;
-    if (ctx->eig.prec != 32) return set_err(ctx, HISQ_ERR_INVALID_ARG, "tensor-core deflation needs FP32 eigenvectors");
+    if (ctx->eig.prec != 32 && ctx->eig.prec != HISQ_PREC_BF16)
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "tensor-core deflation needs FP32 or BF16 eigenvectors");
     tc_release(ctx);
     const size_t L = size_t(3) * Vh;
-    const size_t ld_sm = ((size_t(2) * n + 63) / 64) * 64; // halves per site-major row (128 B multiple)
+    const size_t ld_sm = ((size_t(2) * n + 63) / 64) * 64; // 16-bit values per site-major row (128 B multiple)
+    if (ctx->eig.prec == HISQ_PREC_BF16) {
+        // the stored vectors are the projection operand; build the site-major copy
+        const size_t bytes = L * ld_sm * sizeof(__nv_bfloat16);
+        void *sm = dev_alloc(ctx, bytes);
+        if (!sm) return HISQ_ERR_OOM;
+        HISQ_CUDA(cudaMemsetAsync(sm, 0, bytes, ctx->stream));
+        S.bf16 = true;
+        S.vm_hi = ctx->eig.vecs;
+        S.sm_hi = sm;
+        S.owned = sm;
+        S.ld_sm = ld_sm;
+        S.bytes = bytes;
+        S.n = n;
+        S.Vh = Vh;
+        S.version = ctx->eig.version;
+        S.sigma = 1.f;
+        ctx->launches++;
+        dim3 grid(unsigned((L + 31) / 32), unsigned((n + 31) / 32));
+        k_build_v_sm_bf16<<<grid, dim3(32, 8), 0, ctx->stream>>>(int(L), n, (const __nv_bfloat162 *)ctx->eig.vecs, L,
+                                                                 (__nv_bfloat162 *)sm, ld_sm / 2);
+        HISQ_CUDA(cudaGetLastError());
+        return HISQ_OK;
+    }
     const size_t vm = L * n * 2, sm = L * ld_sm;
     const size_t bytes = (2 * vm + 2 * sm) * sizeof(__half);
     __half *base = (__half *)dev_alloc(ctx, bytes);
     if (!base) return HISQ_ERR_OOM;
     HISQ_CUDA(cudaMemsetAsync(base, 0, bytes, ctx->stream));
+    S.owned = base;
     S.vm_hi = base;
     S.vm_lo = base + vm;
     S.sm_hi = base + 2 * vm;
@@ -409,18 +491,20 @@ static hisq_status tc_prepare_v(hisq_ctx *ctx, int n)
     S.sigma = float(std::sqrt(double(L)));
     ctx->launches++;
     k_build_v<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(Vh, n, (const char *)ctx->eig.vecs, spinor_bytes(32, Vh),
-                                                          S.sigma, S.vm_hi, S.vm_lo, S.sm_hi, S.sm_lo, ld_sm);
+                                                          S.sigma, (__half *)S.vm_hi, (__half *)S.vm_lo,
+                                                          (__half *)S.sm_hi, (__half *)S.sm_lo, ld_sm);
     HISQ_CUDA(cudaGetLastError());
     return HISQ_OK;
 }
 
-template <int MT, int N, int ST, int MODE>
+template <int MT, int N, int ST, int MODE, bool BF16>
 static hisq_status launch_gemm(hisq_ctx *ctx, dim3 grid, const CUtensorMap *m, int K, int kchunk, int Mrows, float *part,
                                ExpandEpi epi, int *status)
 {
-    constexpr int STAGE = 2 * MT * 128 * TC_ROWB + 2 * N * TC_ROWB;
+    constexpr int STAGE = (BF16 ? 1 : 2) * MT * 128 * TC_ROWB + 2 * N * TC_ROWB;
     const size_t smem = size_t(ST) * STAGE + 1024 + 256;
-    auto kern = k_tc_gemm<MT, N, ST, MODE>;
+    static_assert(ST * STAGE + 1024 + 256 <= 227 * 1024, "shared memory");
+    auto kern = k_tc_gemm<MT, N, ST, MODE, BF16>;
     static bool attr = false;
     if (!attr) {
         HISQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
@@ -432,12 +516,45 @@ static hisq_status launch_gemm(hisq_ctx *ctx, dim3 grid, const CUtensorMap *m, i
     return HISQ_OK;
 }
 
+// value a as a 16-bit high part and the 16-bit rounding of the remainder
+// (FP16 via the CUDA host conversions; BF16 by round-to-nearest-even on the
+// FP32 bit pattern: BF16 is the upper half of an FP32)
+static uint16_t bf16_bits(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) return uint16_t(u >> 16); // Inf/NaN: not produced here
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return uint16_t(u >> 16);
+}
+static float bf16_value(uint16_t h)
+{
+    const uint32_t u = uint32_t(h) << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+static void split16(double a, bool bf, uint16_t *hi, uint16_t *lo)
+{
+    if (bf) {
+        *hi = bf16_bits(float(a));
+        *lo = bf16_bits(float(a - double(bf16_value(*hi))));
+    } else {
+        const __half h = __float2half_rn(float(a));
+        const __half l = __float2half_rn(float(a - double(__half2float(h))));
+        std::memcpy(hi, &h, 2);
+        std::memcpy(lo, &l, 2);
+    }
+}
+
 // Batched deflation of k right-hand sides with the first n stored eigenpairs:
 // x_j += sum_i v_i c_ij / lambda_i, r_j -= sum_i v_i c_ij, c = V^dag r.
 // R, X: k FP64 even fields (element s of field j at base + j*fstride + s).
 // rnorm[j] = |r_j| (host values) for the operand scaling.  `field` (host,
-// nullable) maps right-hand side j to field field[j] of R and X.
-hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, const double *rnorm, const int *field)
+// nullable) maps right-hand side j to field field[j] of R and X.  With
+// update_r = false only X is updated (R is then the caller's to recompute).
+hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, const double *rnorm, const int *field,
+                             bool update_r)
 {
     if (k < 1 || k > 32) return set_err(ctx, HISQ_ERR_INVALID_ARG, "tensor-core deflation: 1..32 right-hand sides");
     if (n < 1 || n > 512) return set_err(ctx, HISQ_ERR_INVALID_ARG, "tensor-core deflation: 1..512 eigenpairs");
@@ -451,10 +568,11 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
     const int NP = 64;                        // 2k <= 64 columns, padded by zero fill
     std::vector<float> sc(k);
     for (int j = 0; j < k; j++) sc[j] = rnorm[j] > 0 ? float(std::sqrt(double(L)) / rnorm[j]) : 1.f;
-    const size_t rbytes = size_t(2) * k * L * 2 * sizeof(__half);
+    const bool bf = S.bf16;
+    const size_t rbytes = size_t(2) * k * L * 2 * sizeof(__half); // same size for BF16
     char *w = (char *)get_buf(ctx, BUF_TC_WORK, 2 * rbytes + 4096 + sizeof(float) * 8 * 64);
     if (!w) return HISQ_ERR_OOM;
-    __half *rh = (__half *)w, *rl = (__half *)(w + rbytes);
+    void *rh = w, *rl = w + rbytes;
     float *dscale = (float *)(w + 2 * rbytes);
     int *dfield = (int *)(w + 2 * rbytes + 1024);
     int *status = (int *)(w + 2 * rbytes + 2048);
@@ -464,17 +582,24 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
     HISQ_CUDA(cudaMemcpyAsync(dfield, fl.data(), sizeof(int) * k, cudaMemcpyHostToDevice, ctx->stream));
     HISQ_CUDA(cudaMemsetAsync(status, 0, sizeof(int), ctx->stream));
     ctx->launches++;
-    k_build_r<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(L, k, (const double2 *)R, fstride, dfield, dscale, rh, rl);
+    if (bf)
+        k_build_r_bf16<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(L, k, (const double2 *)R, fstride, dfield, dscale,
+                                                                  (__nv_bfloat16 *)rh, (__nv_bfloat16 *)rl);
+    else
+        k_build_r<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(L, k, (const double2 *)R, fstride, dfield, dscale,
+                                                             (__half *)rh, (__half *)rl);
     HISQ_CUDA(cudaGetLastError());
 
     CUtensorMap mp[4];
     const uint64_t Kp = uint64_t(2) * L;
-    if (!make_tmap(&mp[0], S.vm_hi, Kp, n, Kp * 2, 128) || !make_tmap(&mp[1], S.vm_lo, Kp, n, Kp * 2, 128) ||
-        !make_tmap(&mp[2], rh, Kp, 2 * k, Kp * 2, NP) || !make_tmap(&mp[3], rl, Kp, 2 * k, Kp * 2, NP))
+    const void *alo = bf ? S.vm_hi : S.vm_lo; // BF16: no low part (the map is not read)
+    if (!make_tmap(&mp[0], S.vm_hi, Kp, n, Kp * 2, 128, bf) || !make_tmap(&mp[1], alo, Kp, n, Kp * 2, 128, bf) ||
+        !make_tmap(&mp[2], rh, Kp, 2 * k, Kp * 2, NP, bf) || !make_tmap(&mp[3], rl, Kp, 2 * k, Kp * 2, NP, bf))
         return set_err(ctx, HISQ_ERR_CUDA, "tensor map encoding failed");
-    // split K over about two CTAs per SM
+    // split K over about one CTA per SM; rows per CTA: FP16 hi + lo A tiles of
+    // 256 rows, or BF16 A tiles of 512 rows, with B fit two 80 KB stages
     const int mtiles = (n + 127) / 128;
-    constexpr int MTP = 2; // 256 rows per CTA: hi + lo A tiles and B fit two 80 KB stages
+    const int MTP = bf ? (mtiles >= 4 ? 4 : (mtiles >= 2 ? 2 : 1)) : 2;
     const int mgroups = (mtiles + MTP - 1) / MTP;
     int nsplit = std::max(1, ctx->num_sms / mgroups);
     int kchunk = int(((Kp + nsplit - 1) / nsplit + TC_BK - 1) / TC_BK) * TC_BK;
@@ -484,7 +609,18 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
     double *C = (double *)get_buf(ctx, BUF_TC_C, sizeof(double) * size_t(n) * 2 * k);
     if (!part || !C) return HISQ_ERR_OOM;
     ExpandEpi none{};
-    TRY_HISQ((launch_gemm<MTP, NP, 2, 0>(ctx, dim3(nsplit, mgroups), mp, int(Kp), kchunk, Mrows, part, none, status)));
+    if (bf && MTP == 4)
+        TRY_HISQ((launch_gemm<4, NP, 2, 0, true>(ctx, dim3(nsplit, mgroups), mp, int(Kp), kchunk, Mrows, part, none,
+                                                status)));
+    else if (bf && MTP == 2)
+        TRY_HISQ((launch_gemm<2, NP, 2, 0, true>(ctx, dim3(nsplit, mgroups), mp, int(Kp), kchunk, Mrows, part, none,
+                                                status)));
+    else if (bf)
+        TRY_HISQ((launch_gemm<1, NP, 4, 0, true>(ctx, dim3(nsplit, mgroups), mp, int(Kp), kchunk, Mrows, part, none,
+                                                status)));
+    else
+        TRY_HISQ((launch_gemm<2, NP, 2, 0, false>(ctx, dim3(nsplit, mgroups), mp, int(Kp), kchunk, Mrows, part, none,
+                                                 status)));
     ctx->launches++;
     k_reduce_part<<<(n * 2 * k + 255) / 256, 256, 0, ctx->stream>>>(nsplit, n, Mrows, NP, 2 * k, part, C);
     HISQ_CUDA(cudaGetLastError());
@@ -500,7 +636,7 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
     const int NE = 4 * k;                     // columns of the expansion
     const int NEP = ((NE + 15) / 16) * 16;
     const int ldk = int(S.ld_sm);             // K extent of the expansion (2n padded)
-    std::vector<__half> dh(size_t(NEP) * ldk, __float2half(0.f)), dl(size_t(NEP) * ldk, __float2half(0.f));
+    std::vector<uint16_t> dh(size_t(NEP) * ldk, 0), dl(size_t(NEP) * ldk, 0); // FP16 or BF16 bit patterns
     std::vector<float> esc(4 * k);
     const double sig = S.sigma;
     for (int j = 0; j < k; j++) {
@@ -523,11 +659,13 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
         esc[4 * j + 2] = esc[4 * j + 3] = float(1.0 / (sig * tr));
         auto put = [&](int col, int i, double a_re, double a_im) {
             // K index (i, 0) multiplies Re v_i, (i, 1) multiplies Im v_i
-            const __half hr = __float2half_rn(float(a_re)), hi_ = __float2half_rn(float(a_im));
-            dh[size_t(col) * ldk + 2 * i] = hr;
-            dh[size_t(col) * ldk + 2 * i + 1] = hi_;
-            dl[size_t(col) * ldk + 2 * i] = __float2half_rn(float(a_re - double(__half2float(hr))));
-            dl[size_t(col) * ldk + 2 * i + 1] = __float2half_rn(float(a_im - double(__half2float(hi_))));
+            const double a[2] = {a_re, a_im};
+            for (int q = 0; q < 2; q++) {
+                uint16_t h, l;
+                split16(a[q], bf, &h, &l);
+                dh[size_t(col) * ldk + 2 * i + q] = h;
+                dl[size_t(col) * ldk + 2 * i + q] = l;
+            }
         };
         for (int i = 0; i < n; i++) {
             const double xr = dr[i] * tx, xi = di[i] * tx, rr = cr[i] * tr, ri = ci[i] * tr;
@@ -538,10 +676,10 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
             put(4 * j + 3, i, ri, rr);
         }
     }
-    const size_t dbytes = size_t(NEP) * ldk * sizeof(__half);
+    const size_t dbytes = size_t(NEP) * ldk * sizeof(uint16_t);
     char *dbuf = (char *)get_buf(ctx, BUF_TC_D, 2 * dbytes + sizeof(float) * 4 * 64);
     if (!dbuf) return HISQ_ERR_OOM;
-    __half *ddh = (__half *)dbuf, *ddl = (__half *)(dbuf + dbytes);
+    void *ddh = dbuf, *ddl = dbuf + dbytes;
     float *desc = (float *)(dbuf + 2 * dbytes);
     HISQ_CUDA(cudaMemcpyAsync(ddh, dh.data(), dbytes, cudaMemcpyHostToDevice, ctx->stream));
     HISQ_CUDA(cudaMemcpyAsync(ddl, dl.data(), dbytes, cudaMemcpyHostToDevice, ctx->stream));
@@ -549,16 +687,24 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
     // the TMA box of D' is as tall as the kernel's N (rows beyond NEP are zero filled)
     const int NT = NEP <= 32 ? 32 : (NEP <= 64 ? 64 : 128);
     CUtensorMap me[4];
-    if (!make_tmap(&me[0], S.sm_hi, ldk, L, S.ld_sm * 2, 128) || !make_tmap(&me[1], S.sm_lo, ldk, L, S.ld_sm * 2, 128) ||
-        !make_tmap(&me[2], ddh, ldk, NEP, size_t(ldk) * 2, NT) || !make_tmap(&me[3], ddl, ldk, NEP, size_t(ldk) * 2, NT))
+    const void *slo = bf ? S.sm_hi : S.sm_lo;
+    if (!make_tmap(&me[0], S.sm_hi, ldk, L, S.ld_sm * 2, 128, bf) || !make_tmap(&me[1], slo, ldk, L, S.ld_sm * 2, 128, bf) ||
+        !make_tmap(&me[2], ddh, ldk, NEP, size_t(ldk) * 2, NT, bf) ||
+        !make_tmap(&me[3], ddl, ldk, NEP, size_t(ldk) * 2, NT, bf))
         return set_err(ctx, HISQ_ERR_CUDA, "tensor map encoding failed");
-    ExpandEpi epi{(double2 *)X, (double2 *)R, fstride, desc, dfield, k, L};
+    ExpandEpi epi{(double2 *)X, update_r ? (double2 *)R : nullptr, fstride, desc, dfield, k, L};
     const int ntiles = (L + 127) / 128;
     const int grid = std::min(ntiles, ctx->num_sms);
     hisq_status st;
-    if (NT == 32) st = launch_gemm<1, 32, 4, 1>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
-    else if (NT == 64) st = launch_gemm<1, 64, 4, 1>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
-    else st = launch_gemm<1, 128, 3, 1>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
+    if (bf) {
+        if (NT == 32) st = launch_gemm<1, 32, 4, 1, true>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
+        else if (NT == 64) st = launch_gemm<1, 64, 4, 1, true>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
+        else st = launch_gemm<1, 128, 4, 1, true>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
+    } else {
+        if (NT == 32) st = launch_gemm<1, 32, 4, 1, false>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
+        else if (NT == 64) st = launch_gemm<1, 64, 4, 1, false>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
+        else st = launch_gemm<1, 128, 3, 1, false>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
+    }
     if (st != HISQ_OK) return st;
     HISQ_CUDA(cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -596,7 +742,7 @@ extern "C" hisq_status hisq_deflate_batch(hisq_ctx *ctx, int n, int nrhs, const 
         norms[j] = std::sqrt(n2);
     }
     HISQ_CUDA(cudaMemsetAsync(X, 0, s64 * nrhs, ctx->stream));
-    TRY_HISQ(tc_deflate_batch(ctx, n, nrhs, (double *)R, (double *)X, norms.data(), nullptr));
+    TRY_HISQ(tc_deflate_batch(ctx, n, nrhs, (double *)R, (double *)X, norms.data(), nullptr, true));
     for (int j = 0; j < nrhs; j++) {
         HISQ_CUDA(cudaMemsetAsync(f, 0, full, ctx->stream));
         TRY_HISQ(launch_scatter_parity(ctx, X + s64 * j, 64, 0, f));

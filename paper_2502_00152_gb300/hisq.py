@@ -29,6 +29,12 @@ HISQ_ERR_NUMERICAL = 5
 HISQ_ERR_TIMEOUT = 6
 HISQ_ERR_STATE = 7
 
+# storage precisions (hisq_precision)
+HISQ_PREC_DOUBLE = 64
+HISQ_PREC_SINGLE = 32
+HISQ_PREC_HALF = 16
+HISQ_PREC_BF16 = 15  # eigenvector storage only
+
 
 class HisqError(RuntimeError):
     def __init__(self, status: int, message: str):
