@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--learned-pairs", type=int, default=512)
     ap.add_argument("--learned-epochs", type=int, default=30)
     ap.add_argument("--learned-lr", type=float, default=2e-3)
+    ap.add_argument("--sweep", choices=["delta_tr", "mass"], default=None,
+                    help="precision/re-deflation sweep (Fig. 2 analogue) or iterations vs mass (Fig. 1 analogue) "
+                         "on the 32^3x64 lattice; prints one JSON line per table")
     ap.add_argument("--rhs-per-step", type=int, default=None,
                     help="right-hand sides solved together per step (batched); default 1, 24 for c3")
     return ap.parse_args()
@@ -565,10 +568,89 @@ def _even_rhs(H, ctx, eta, m, par_np):
     return y
 
 
+# ------------------------------------------------------------ sweeps
+def run_sweep(a):
+    """32^3x64, m = 0.002 (seed 2, eps 0.3), Gaussian sources, single-RHS solves
+    to the 1e-10 FP64 true residual.
+    delta_tr: re-deflation threshold x eigenvector storage (FP32, BF16) with
+    256 eigenpairs; delta_tr = 0 switches re-deflation off (Fig. 2 analogue).
+    mass: plain and deflated CG iterations and time per RHS against the quark
+    mass, with one set of massless eigenpairs (lambda_i = eps_i + 4 m^2; Fig. 1
+    analogue)."""
+    import numpy as np
+    import torch
+
+    from paper_2502_00152_gb300 import build as B
+    from paper_2502_00152_gb300 import hisq as H
+    from paper_2502_00152_gb300 import inputs as I
+
+    B.build()
+    cfg = I.lattice_config("c2")
+    dims, m0 = cfg["dims"], cfg["mass"]
+    fat, lng = I.hisq_links(dims, cfg["seed"], cfg["eps"])
+    stream = torch.cuda.current_stream()
+    ctx = H.hisq_create(dims, t_antiperiodic=True, device=0, cuda_stream=stream.cuda_stream)
+    H.hisq_load_links(ctx, fat, lng, long_recon=a.recon, long_scale=I.C3_NAIK if a.recon == 12 else 1.0)
+    del fat, lng
+    H.hisq_set_mass(ctx, m0)
+    n_ev = a.n_ev if a.n_ev is not None else 256
+    srcs = [torch.from_numpy(I.gaussian_source(dims, SOURCE_SEED, 500 + k)).cuda() for k in range(2)]
+    psi = torch.zeros_like(srcs[0])
+
+    def eigensolve(prec):
+        ep = H.hisq_default_eig_params(n_ev=n_ev, n_kr=max(int(1.5 * n_ev), n_ev + 32), tol=a.eig_tol,
+                                       max_restarts=100, cheby_degree=a.cheby, a_min=a.amin, storage_precision=prec)
+        t0 = time.time()
+        H.hisq_eigensolve(ctx, ep)
+        torch.cuda.synchronize()
+        return time.time() - t0
+
+    def solve(prm):
+        out = []
+        for e in srcs:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, status = H.hisq_solve_device(ctx, e, psi, 1, prm)
+            torch.cuda.synchronize()
+            out.append(dict(ms=(time.perf_counter() - t0) * 1e3, iterations=st[0]["iterations"],
+                            redeflations=st[0]["redeflations"], reliable_updates=st[0]["reliable_updates"],
+                            full_residual=st[0]["full_residual"], status=int(status)))
+        return dict(ms_per_rhs=round(float(np.mean([o["ms"] for o in out])), 2),
+                    iterations=[o["iterations"] for o in out], redeflations=[o["redeflations"] for o in out],
+                    reliable_updates=[o["reliable_updates"] for o in out],
+                    true_residual_max=max(o["full_residual"] for o in out), status=[o["status"] for o in out])
+
+    base = dict(tol=1e-10, precision_sloppy=a.sloppy, link_precision_sloppy=a.links, compute_full_residual=1)
+    if a.sweep == "delta_tr":
+        rows = []
+        for prec, name in ((32, "FP32"), (15, "BF16")):
+            t_eig = eigensolve(prec)
+            solve(H.hisq_default_solve_params(deflate=1, **base))  # warm-up
+            for dtr in (0.0, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6):
+                r = solve(H.hisq_default_solve_params(deflate=1, delta_tr=dtr, max_iter=20000, **base))
+                rows.append(dict(eigvecs=name, delta_tr=dtr, **r))
+            rows.append(dict(eigvecs=name, eigensolve_seconds=round(t_eig, 1)))
+        plain = solve(H.hisq_default_solve_params(deflate=0, **base))
+        print(json.dumps({"sweep": "delta_tr", "lattice": list(dims), "mass": m0, "n_ev": n_ev,
+                          "plain_cg": plain, "rows": rows}), flush=True)
+    else:
+        eigensolve(32)
+        rows = []
+        for m in (0.05, 0.02, 0.01, 0.005, 0.002, 0.001, 0.0005):
+            H.hisq_set_mass(ctx, m)
+            p = solve(H.hisq_default_solve_params(deflate=0, max_iter=20000, **base))
+            d = solve(H.hisq_default_solve_params(deflate=1, max_iter=20000, **base))
+            rows.append(dict(mass=m, plain=p, deflated=d))
+        print(json.dumps({"sweep": "mass", "lattice": list(dims), "n_ev": n_ev, "rows": rows}), flush=True)
+    ctx.close()
+
+
 if __name__ == "__main__":
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        run_sweep(args)
     elif args.learned:
         run_learned(args)
     else:

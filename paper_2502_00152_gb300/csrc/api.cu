@@ -22,6 +22,16 @@ int log_level()
     return lvl;
 }
 
+bool tuning_enabled()
+{
+    static int on = -1;
+    if (on < 0) {
+        const char *e = getenv("HISQ_TUNE");
+        on = (e && atoi(e) == 0) ? 0 : 1;
+    }
+    return on;
+}
+
 bool graphs_enabled(const hisq_ctx *ctx)
 {
     static int on = -1;

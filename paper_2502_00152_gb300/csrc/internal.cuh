@@ -10,6 +10,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <map>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -618,6 +619,9 @@ struct hisq_ctx {
     double *bmonitor_d = nullptr;
     int bmonitor_len = 4096;
 
+    // launch shapes chosen by the autotuner, by problem key
+    std::map<unsigned long long, int> tuned;
+
     // scratch buffers (grown on demand)
     void *bufs[hisq::BUF_COUNT] = {};
     size_t buf_cap[hisq::BUF_COUNT] = {};
@@ -719,6 +723,68 @@ hisq_status graph_run(hisq_ctx *ctx, IterGraphs &G, int slot, long long key, F &
     ctx->launches += G.launches[slot];
     cudaError_t e = cudaGraphLaunch(G.exec[slot], ctx->stream);
     if (e != cudaSuccess) return cuda_err(ctx, e, "graph launch");
+    return HISQ_OK;
+}
+
+// ------------------------------------------------------------ autotuner
+// Launch-shape autotuning: `launch(i)` enqueues candidate i (0 <= i < n) of an
+// idempotent launch (same inputs, same outputs whichever shape runs it).  On
+// the first call for `key` each candidate is run once to warm up and twice
+// timed with CUDA events; the fastest index is kept in the context and used
+// from then on.  Not while the stream is being captured (the default index is
+// used then, and not remembered), nor with HISQ_TUNE=0.
+bool tuning_enabled();
+
+template <class F>
+hisq_status autotune(hisq_ctx *ctx, unsigned long long key, int n, int dflt, F &&launch, int *chosen)
+{
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) {
+        *chosen = it->second;
+        return HISQ_OK;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusActive;
+    if (!tuning_enabled() || cs != cudaStreamCaptureStatusNone || n <= 1) {
+        *chosen = dflt;
+        if (cs == cudaStreamCaptureStatusNone) ctx->tuned[key] = dflt;
+        return HISQ_OK;
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return cuda_err(ctx, cudaGetLastError(), "tuner event");
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_err(ctx, cudaGetLastError(), "tuner event");
+    }
+    int best = dflt;
+    float best_ms = 1e30f;
+    hisq_status st = HISQ_OK;
+    for (int i = 0; i < n && st == HISQ_OK; i++) {
+        st = launch(i);
+        if (st != HISQ_OK) break;
+        cudaEventRecord(e0, ctx->stream);
+        st = launch(i);
+        if (st == HISQ_OK) st = launch(i);
+        cudaEventRecord(e1, ctx->stream);
+        if (st != HISQ_OK) break;
+        float ms = 0;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            st = cuda_err(ctx, cudaGetLastError(), "tuner timing");
+            break;
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != HISQ_OK) return st;
+    if (log_level() > 0)
+        fprintf(stderr, "[hisq] autotune key %llx: candidate %d of %d (%.3f ms per launch)\n", key, best, n,
+                best_ms / 2);
+    ctx->tuned[key] = best;
+    *chosen = best;
     return HISQ_OK;
 }
 

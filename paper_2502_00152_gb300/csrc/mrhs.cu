@@ -9,6 +9,7 @@
 // Per-RHS reductions are deterministic: lanes by a fixed shuffle tree, warps in
 // a fixed order, blocks by the last block in block order.
 #include <algorithm>
+#include <functional>
 
 #include "internal.cuh"
 
@@ -277,17 +278,38 @@ __global__ void __launch_bounds__(512, 1)
 }
 
 // ------------------------------------------------------------- launch glue
-// right-hand sides per thread: four keeps the link matrices, four accumulators
-// and eight gathered neighbours in registers (128 per thread) with all gathers
-// of a hop issued together
-constexpr int kMrhsR = 4;
+// Launch shapes of the batched kernels, tried by the autotuner on the first
+// D_oe launch of each (batch size, precision, link format): R right-hand
+// sides per thread (2, 3 or 4: more spills the link matrices, accumulators and
+// gathers out of 128 registers) and 1 or 2 site groups per block (up to 512
+// threads).  Candidate 0, R = 4 with blocks of about 8 warps, is the default.
+struct MrhsShape {
+    int R;
+    MrhsTile tile;
+};
 
-static MrhsTile mrhs_tile(int kact, int R)
+static int mrhs_candidates(int kact, MrhsShape *out)
 {
-    MrhsTile t;
-    t.nch = std::max(1, (kact + R - 1) / R); // <= 16 for kact <= kMaxBatch = 64
-    t.nsg = std::max(1, 8 / t.nch);          // blocks of 8 warps, up to 16 when nch > 8
-    return t;
+    int n = 0;
+    for (int R : {4, 3, 2}) {
+        const int nch = (kact + R - 1) / R;
+        if (nch > 16) continue;
+        const int nsg0 = std::max(1, 8 / nch);
+        for (int nsg : {nsg0, 2 * nsg0}) {
+            if (32 * nch * nsg > 512 || nsg > 8) continue; // batch_reduce holds 8 site groups
+            out[n].R = R;
+            out[n].tile.nch = nch;
+            out[n].tile.nsg = nsg;
+            n++;
+        }
+    }
+    return n;
+}
+
+static unsigned long long mrhs_key(const hisq_ctx *ctx, int kact, int prec)
+{
+    return (1ull << 40) | (unsigned long long)kact | ((unsigned long long)prec << 8) |
+           ((unsigned long long)ctx->long_recon << 16);
 }
 
 // blocks per SM of `kern` at `threads` threads, cached per kernel and shape
@@ -327,10 +349,10 @@ struct LinksFvB {
 };
 
 template <int R, class S, class Epi>
-static hisq_status run_mrhs_r(hisq_ctx *ctx, int par, const BatchF<S> &in, int kact, const Epi &epi, BatchRed br)
+static hisq_status run_mrhs_r(hisq_ctx *ctx, int par, const BatchF<S> &in, const MrhsTile &tl, const Epi &epi,
+                              BatchRed br)
 {
     const int Vh = ctx->g.Vh;
-    const MrhsTile tl = mrhs_tile(kact, R);
     const int threads = 32 * tl.nch * tl.nsg;
     LinksFvB L{ctx->links_f[par], Vh, ctx->long_recon == 12 ? 1 : 2};
     auto launch = [&](auto kern, auto L12) -> hisq_status {
@@ -347,12 +369,47 @@ static hisq_status run_mrhs_r(hisq_ctx *ctx, int par, const BatchF<S> &in, int k
 }
 
 template <class S, class Epi>
-static hisq_status run_mrhs(hisq_ctx *ctx, int par, int link_prec, const BatchF<S> &in, int kact, const Epi &epi,
-                            BatchRed br)
+static hisq_status run_shape(hisq_ctx *ctx, int par, const BatchF<S> &in, const MrhsShape &sh, const Epi &epi,
+                             BatchRed br)
+{
+    switch (sh.R) {
+    case 2: return run_mrhs_r<2>(ctx, par, in, sh.tile, epi, br);
+    case 3: return run_mrhs_r<3>(ctx, par, in, sh.tile, epi, br);
+    default: return run_mrhs_r<4>(ctx, par, in, sh.tile, epi, br);
+    }
+}
+
+// the shape for this batch: tuned on an idempotent launch (may_tune), else
+// the one tuned before, else the default
+static hisq_status mrhs_shape(hisq_ctx *ctx, int kact, int prec, MrhsShape *sh, bool may_tune,
+                              const std::function<hisq_status(const MrhsShape &)> &launch)
+{
+    MrhsShape cand[16];
+    const int n = mrhs_candidates(kact, cand);
+    int idx = 0;
+    const unsigned long long key = mrhs_key(ctx, kact, prec);
+    if (may_tune) {
+        hisq_status st = autotune(ctx, key, n, 0, [&](int i) { return launch(cand[i]); }, &idx);
+        if (st != HISQ_OK) return st;
+    } else {
+        auto it = ctx->tuned.find(key);
+        if (it != ctx->tuned.end()) idx = it->second;
+    }
+    *sh = cand[idx < n ? idx : 0];
+    return HISQ_OK;
+}
+
+template <class S, class Epi>
+static hisq_status run_mrhs(hisq_ctx *ctx, int par, int link_prec, int prec, const BatchF<S> &in, int kact,
+                            const Epi &epi, BatchRed br, bool may_tune)
 {
     if (link_prec != 32) return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched operator: FP32 links only");
     if (kact < 1 || kact > kMaxBatch) return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched operator: 1..64 right-hand sides");
-    return run_mrhs_r<kMrhsR>(ctx, par, in, kact, epi, br);
+    MrhsShape sh;
+    hisq_status st = mrhs_shape(ctx, kact, prec, &sh, may_tune,
+                                [&](const MrhsShape &c) { return run_shape(ctx, par, in, c, epi, br); });
+    if (st != HISQ_OK) return st;
+    return run_shape(ctx, par, in, sh, epi, br);
 }
 
 BatchRed batch_red(hisq_ctx *ctx, int op)
@@ -373,8 +430,12 @@ hisq_status launch_mrhs_dslash_tt(hisq_ctx *ctx, int prec, int link_prec, void *
     const int Vh = ctx->g.Vh;
     BatchRed br = batch_red(ctx, BFIN_ALPHA);
     switch (prec) {
-    case 32: return run_mrhs(ctx, 1, link_prec, batchf<SpinorF>(p, Vh, 32), kact, BEpiStore<SpinorF>{batchf<SpinorF>(tmp, Vh, 32)}, br);
-    case 16: return run_mrhs(ctx, 1, link_prec, batchf<SpinorH>(p, Vh, 16), kact, BEpiStore<SpinorH>{batchf<SpinorH>(tmp, Vh, 16)}, br);
+    case 32:
+        return run_mrhs(ctx, 1, link_prec, 32, batchf<SpinorF>(p, Vh, 32), kact,
+                        BEpiStore<SpinorF>{batchf<SpinorF>(tmp, Vh, 32)}, br, true);
+    case 16:
+        return run_mrhs(ctx, 1, link_prec, 16, batchf<SpinorH>(p, Vh, 16), kact,
+                        BEpiStore<SpinorH>{batchf<SpinorH>(tmp, Vh, 16)}, br, true);
     }
     return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched sloppy precision must be 32 or 16");
 }
@@ -388,22 +449,21 @@ hisq_status launch_mrhs_dslash_update(hisq_ctx *ctx, int prec, int link_prec, vo
     switch (prec) {
     case 32: {
         BEpiCG<SpinorF, SpinorF> epi{batchf<SpinorF>(p, Vh, 32), batchf<SpinorF>(r, Vh, 32), batchf<SpinorF>(x, Vh, 32), ctx->bscal};
-        return run_mrhs(ctx, 0, link_prec, batchf<SpinorF>(tmp, Vh, 32), kact, epi, br);
+        return run_mrhs(ctx, 0, link_prec, 32, batchf<SpinorF>(tmp, Vh, 32), kact, epi, br, false);
     }
     case 16: {
         BEpiCG<SpinorH, SpinorF> epi{batchf<SpinorH>(p, Vh, 16), batchf<SpinorH>(r, Vh, 16), batchf<SpinorF>(x, Vh, 32), ctx->bscal};
-        return run_mrhs(ctx, 0, link_prec, batchf<SpinorH>(tmp, Vh, 16), kact, epi, br);
+        return run_mrhs(ctx, 0, link_prec, 16, batchf<SpinorH>(tmp, Vh, 16), kact, epi, br, false);
     }
     }
     return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched sloppy precision must be 32 or 16");
 }
 
-// (3) p_j = r_j + beta_j p_j, pp_j
+// (3) p_j = r_j + beta_j p_j, pp_j (the shape of the batch's Dslash)
 template <int R, class S>
-static hisq_status run_p_update(hisq_ctx *ctx, void *r, void *p, int kact, int prec)
+static hisq_status run_p_update(hisq_ctx *ctx, void *r, void *p, const MrhsTile &tl, int prec)
 {
     const int Vh = ctx->g.Vh;
-    const MrhsTile tl = mrhs_tile(kact, R);
     const int threads = 32 * tl.nch * tl.nsg;
     auto kern = k_p_update_mrhs<R, S>;
     const int grid = grid_for(ctx, long(Vh), 32 * tl.nsg, mrhs_blocks_per_sm(kern, threads));
@@ -417,11 +477,19 @@ static hisq_status run_p_update(hisq_ctx *ctx, void *r, void *p, int kact, int p
 hisq_status launch_mrhs_p_update(hisq_ctx *ctx, int prec, void *r, void *p, int kact)
 {
     if (kact < 1 || kact > kMaxBatch) return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched p update: 1..64 right-hand sides");
-    switch (prec) {
-    case 32: return run_p_update<kMrhsR, SpinorF>(ctx, r, p, kact, 32);
-    case 16: return run_p_update<kMrhsR, SpinorH>(ctx, r, p, kact, 16);
-    }
-    return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched sloppy precision must be 32 or 16");
+    if (prec != 32 && prec != 16) return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched sloppy precision must be 32 or 16");
+    MrhsShape sh;
+    hisq_status st = mrhs_shape(ctx, kact, prec, &sh, false, nullptr);
+    if (st != HISQ_OK) return st;
+    auto go = [&](auto tagS) -> hisq_status {
+        typedef decltype(tagS) S;
+        switch (sh.R) {
+        case 2: return run_p_update<2, S>(ctx, r, p, sh.tile, prec);
+        case 3: return run_p_update<3, S>(ctx, r, p, sh.tile, prec);
+        default: return run_p_update<4, S>(ctx, r, p, sh.tile, prec);
+        }
+    };
+    return prec == 32 ? go(SpinorF{}) : go(SpinorH{});
 }
 
 } // namespace hisq
