@@ -66,7 +66,7 @@ def parse():
                     help="precision/re-deflation sweep (Fig. 2 analogue) or iterations vs mass (Fig. 1 analogue) "
                          "on the 32^3x64 lattice; prints one JSON line per table")
     ap.add_argument("--rhs-per-step", type=int, default=None,
-                    help="right-hand sides solved together per step (batched); default 1, 24 for c3")
+                    help="right-hand sides solved together per step (batched); default 1, 24 for c3, 12 for c5")
     return ap.parse_args()
 
 
@@ -202,7 +202,7 @@ def run_ours(a):
     Vh = V // 2
     n_ev = a.n_ev if a.n_ev is not None else cfg.get("n_ev", 0)
     if a.eig_prec is None:
-        a.eig_prec = 15 if a.config == "c3" else 32
+        a.eig_prec = 15 if a.config in ("c3", "c5") else 32
     eig_name = {32: "FP32", 16: "FP16", 15: "BF16"}.get(a.eig_prec, str(a.eig_prec))
     n_kr = a.n_kr if a.n_kr is not None else max(int(1.5 * n_ev), n_ev + 32)
 
@@ -228,10 +228,14 @@ def run_ours(a):
 
     # sources: resident in HBM before the timed region (FP64 full-lattice fields)
     keep_links = (fat, lng) if (rank == 0 and world == 1 and not a.no_cpu_baseline) else (None, None)
-    kps = a.rhs_per_step if a.rhs_per_step is not None else (24 if a.config == "c3" else 1)
+    kps = a.rhs_per_step if a.rhs_per_step is not None else {"c3": 24, "c5": 12}.get(a.config, 1)
     nsrc = a.warmup + a.steps
     if kps == 1:
         srcs = [I.gaussian_source(dims, SOURCE_SEED, rank * 1000 + k) for k in range(nsrc)]
+    elif a.config == "c5":
+        # Gaussian sources x 3 colours (colour-diluted)
+        srcs = [np.stack([I.gaussian_colour_source(dims, SOURCE_SEED, (rank * 1000 + k) * 64 + q // 3, q % 3)
+                          for q in range(kps)]) for k in range(nsrc)]
     else:
         # Z2 wall sources: 8 timeslices x 3 colours per 24 right-hand sides
         srcs = [np.stack([I.z2_wall_source(dims, SOURCE_SEED + 97 * (rank * 1000 + k) + q // 24, (q % 24) // 3, q % 3)
@@ -371,7 +375,9 @@ def run_ours(a):
             "workload": f"HISQ {dims[0]}^3x{dims[3]}, m={m}, {n_ev} eigenpairs ({eig_name}), deflated "
                         f"mixed-precision CG (FP{a.sloppy} vectors, FP{a.links} links recon {a.recon}, FP64 "
                         f"reliable updates), "
-                        + ("1 Gaussian RHS per step" if kps == 1 else f"{kps} Z2 wall RHS per step, batched")
+                        + ("1 Gaussian RHS per step" if kps == 1 else
+                           (f"{kps} RHS per step ({kps // 3} Gaussian sources x 3 colours), batched"
+                            if a.config == "c5" else f"{kps} Z2 wall RHS per step, batched"))
                         + f", tol {tol}",
             "rhs_per_step": kps,
             "lattice": list(dims), "mass": m, "n_ev": n_ev, "sloppy_vectors": f"fp{a.sloppy}",

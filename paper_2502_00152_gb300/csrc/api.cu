@@ -294,14 +294,9 @@ hisq_status hisq_load_links(hisq_ctx *ctx, const double *fat, const double *lng,
     for (int p = 0; p < 2; p++) {
         ctx->links_d[p] = (double2 *)dev_alloc(ctx, size_t(Vh) * 16 * 9 * 16);
         ctx->links_f[p] = (float4 *)dev_alloc(ctx, size_t(Vh) * (long_recon == 12 ? 4 : 8) * 9 * 16);
-        ctx->links_h[p] = (uint2 *)dev_alloc(ctx, size_t(Vh) * (long_recon == 12 ? 4 : 8) * 9 * 8);
-        if (long_recon == 12) {
-            ctx->links_f12[p] = (float4 *)dev_alloc(ctx, size_t(Vh) * 4 * 6 * 16);
-            ctx->links_h12[p] = (uint2 *)dev_alloc(ctx, size_t(Vh) * 4 * 6 * 8);
-        }
-        if (!ctx->links_d[p] || !ctx->links_f[p] || !ctx->links_h[p] ||
-            (long_recon == 12 && (!ctx->links_f12[p] || !ctx->links_h12[p])))
-            return HISQ_ERR_OOM;
+        if (long_recon == 12) ctx->links_f12[p] = (float4 *)dev_alloc(ctx, size_t(Vh) * 4 * 6 * 16);
+        if (!ctx->links_d[p] || !ctx->links_f[p] || (long_recon == 12 && !ctx->links_f12[p])) return HISQ_ERR_OOM;
+        // FP16 links are built from the FP32 ones on first use (ensure_half_links)
     }
     ctx->long_recon = long_recon;
     ctx->long_scale = long_recon == 12 ? long_scale : 1.0;

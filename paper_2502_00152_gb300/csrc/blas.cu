@@ -2,6 +2,8 @@
 // products with deterministic grid reductions, the CG direction update, the
 // deflation projection and expansion of Eq. 4 (x = sum_i v_i lambda_i^-1 v_i^dag b),
 // and the Ritz basis rotation of the thick-restart Lanczos eigensolver.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace hisq {
@@ -505,12 +507,13 @@ hisq_status launch_defl_scale(hisq_ctx *ctx, int n, double *c_dev, const double 
 
 // ------------------------------------------------------------- basis rotation
 // Out (Lf x k_out) = In (Lf x k_in) * Y (k_in x k_out), vectors are columns of
-// Lf = 6 Vh floats (FP32 colour-vector storage), Y real (FP64 row major).
+// Lf floats (rows of FP32 colour-vector storage; ld / ld_out floats between
+// columns), Y real (FP64 row major).
 constexpr int RBM = 128, RBN = 64, RBK = 16;
 
 __global__ void __launch_bounds__(256)
     k_rotate(int Lf, int k_in, int k_out, const float *__restrict__ In, size_t ld, const double *__restrict__ Y,
-             float *__restrict__ Out)
+             float *__restrict__ Out, size_t ld_out)
 {
     __shared__ __align__(16) float As[RBK][RBM];
     __shared__ __align__(16) float Bs[RBK][RBN];
@@ -562,20 +565,32 @@ __global__ void __launch_bounds__(256)
     for (int j = 0; j < 4; j++) {
         const int c = n0 + ty * 4 + j;
         if (c >= k_out) continue;
-        float *dst = Out + size_t(c) * ld + m0 + tx * 8;
+        float *dst = Out + size_t(c) * ld_out + m0 + tx * 8;
         if (m0 + tx * 8 + 3 < Lf) *reinterpret_cast<float4 *>(dst) = make_float4(acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
         if (m0 + tx * 8 + 7 < Lf) *reinterpret_cast<float4 *>(dst + 4) = make_float4(acc[4][j], acc[5][j], acc[6][j], acc[7][j]);
     }
 }
 
-hisq_status launch_rotate(hisq_ctx *ctx, int k_in, int k_out, const void *Vin, const double *Y_dev, void *Vout)
+// V[:, 0..k_out) = V[:, 0..k_in) Y in place (k_out <= k_in): rows of V are taken
+// in chunks of `chunk` floats (a multiple of RBM), each chunk rotated into
+// `tmp` (k_out x chunk floats) and copied back, so no second basis is needed.
+hisq_status launch_rotate_inplace(hisq_ctx *ctx, int k_in, int k_out, void *V, const double *Y_dev, float *tmp,
+                                  int chunk)
 {
     const int Lf = 6 * ctx->g.Vh;
-    const size_t ld = size_t(ctx->g.Vh) * 6; // floats between vectors (24 B per site)
-    dim3 grid((Lf + RBM - 1) / RBM, (k_out + RBN - 1) / RBN);
-    ctx->launches++;
-    k_rotate<<<grid, 256, 0, ctx->stream>>>(Lf, k_in, k_out, (const float *)Vin, ld, Y_dev, (float *)Vout);
-    LAUNCH_CHECK("rotate");
+    const size_t ld = size_t(ctx->g.Vh) * 6;
+    if (k_out > k_in || chunk < RBM || chunk % RBM) return set_err(ctx, HISQ_ERR_INVALID_ARG, "in-place rotation shape");
+    for (int m0 = 0; m0 < Lf; m0 += chunk) {
+        const int len = std::min(chunk, Lf - m0);
+        dim3 grid((len + RBM - 1) / RBM, (k_out + RBN - 1) / RBN);
+        ctx->launches++;
+        k_rotate<<<grid, 256, 0, ctx->stream>>>(len, k_in, k_out, (const float *)V + m0, ld, Y_dev, tmp, size_t(chunk));
+        LAUNCH_CHECK("rotate chunk");
+        cudaError_t e = cudaMemcpy2DAsync((float *)V + m0, ld * sizeof(float), tmp, size_t(chunk) * sizeof(float),
+                                          size_t(len) * sizeof(float), size_t(k_out), cudaMemcpyDeviceToDevice,
+                                          ctx->stream);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "rotate copy-back");
+    }
     return HISQ_OK;
 }
 

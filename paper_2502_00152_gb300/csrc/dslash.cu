@@ -245,6 +245,10 @@ static hisq_status run_any(hisq_ctx *ctx, int par, int link_prec, const S &in, c
             return run_dslash<S, LinksFv, LinksF12, false>(ctx, par, L, LinksF12{nullptr, Vh}, in, epi, ra, dored);
         }
         if (link_prec == 16) {
+            if (!ctx->links_h[par]) {
+                const hisq_status hs = ensure_half_links(ctx);
+                if (hs != HISQ_OK) return hs;
+            }
             LinksHv L{ctx->links_h[par], Vh, nk};
             if (r12) return run_dslash<S, LinksHv, LinksH12, true>(ctx, par, L, LinksH12{ctx->links_h12[par], Vh}, in, epi, ra, dored);
             return run_dslash<S, LinksHv, LinksH12, false>(ctx, par, L, LinksH12{nullptr, Vh}, in, epi, ra, dored);

@@ -272,9 +272,14 @@ static hisq_status trlm(hisq_ctx *ctx, const hisq_eig_params *P, int *n_conv, do
         return set_err(ctx, HISQ_ERR_INVALID_ARG, "storage_precision must be 32, 16 or 15 (BF16)");
     if (!(P->tol > 0)) return set_err(ctx, HISQ_ERR_INVALID_ARG, "tol must be positive");
 
-    // basis (n_kr + 1 vectors), rotation output (n_keep), work
+    // basis (n_kr + 1 vectors, Ritz vectors rotated into its head in place,
+    // through a chunk buffer of about 256 MB), work
+    const int nrot = std::max(n_keep, n_ev);
+    const size_t Lf = size_t(6) * Vh;
+    size_t chunk = (size_t(256) << 20) / (sizeof(float) * size_t(nrot));
+    chunk = std::max<size_t>(128, std::min(Lf, chunk) / 128 * 128);
     char *B = (char *)dev_alloc(ctx, sf * (n_kr + 1));
-    char *R = (char *)dev_alloc(ctx, sf * std::max(n_keep, n_ev));
+    char *R = (char *)dev_alloc(ctx, sizeof(float) * chunk * nrot);
     char *wk = (char *)dev_alloc(ctx, sf * 4);
     double *coef = (double *)dev_alloc(ctx, sizeof(double) * 2 * (n_kr + 1));
     double *Yd = (double *)dev_alloc(ctx, sizeof(double) * size_t(n_kr) * std::max(n_keep, n_ev));
@@ -287,7 +292,7 @@ static hisq_status trlm(hisq_ctx *ctx, const hisq_eig_params *P, int *n_conv, do
             cudaStreamSynchronize(c->stream);
             for (int i = 0; i < 5; i++) dev_free(c, p[i], s[i]);
         }
-    } guard{ctx, {B, R, wk, coef, Yd}, {sf * (n_kr + 1), sf * std::max(n_keep, n_ev), sf * 4, sizeof(double) * 2 * (n_kr + 1), sizeof(double) * size_t(n_kr) * std::max(n_keep, n_ev)}};
+    } guard{ctx, {B, R, wk, coef, Yd}, {sf * (n_kr + 1), sizeof(float) * chunk * nrot, sf * 4, sizeof(double) * 2 * (n_kr + 1), sizeof(double) * size_t(n_kr) * nrot}};
     if (!B || !R || !wk || !coef || !Yd) return HISQ_ERR_OOM;
     void *tmp_odd = get_buf(ctx, BUF_TMP, spinor_bytes(32, Vh));
     if (!tmp_odd) return HISQ_ERR_OOM;
@@ -421,10 +426,9 @@ static hisq_status trlm(hisq_ctx *ctx, const hisq_eig_params *P, int *n_conv, do
         for (int r = 0; r < n_kr; r++)
             for (int c = 0; c < nout; c++) Y[size_t(r) * nout + c] = Z[size_t(r) * n_kr + order[c]];
         HISQ_CUDA(cudaMemcpyAsync(Yd, Y.data(), sizeof(double) * Y.size(), cudaMemcpyHostToDevice, ctx->stream));
-        TRY(launch_rotate(ctx, n_kr, nout, B, Yd, R));
+        TRY(launch_rotate_inplace(ctx, n_kr, nout, B, Yd, (float *)R, int(chunk)));
         if (done) break;
-        // thick restart: v_0..v_{k-1} <- Ritz vectors, v_k <- v_{n_kr}
-        HISQ_CUDA(cudaMemcpyAsync(B, R, sf * n_keep, cudaMemcpyDeviceToDevice, ctx->stream));
+        // thick restart: v_0..v_{k-1} = Ritz vectors (rotated in place), v_k <- v_{n_kr}
         HISQ_CUDA(cudaMemcpyAsync(vec(n_keep), vec(n_kr), sf, cudaMemcpyDeviceToDevice, ctx->stream));
         k = n_keep;
         theta_keep.resize(k);
@@ -436,8 +440,8 @@ static hisq_status trlm(hisq_ctx *ctx, const hisq_eig_params *P, int *n_conv, do
         HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
     }
     HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
-    // R holds the n_ev wanted Ritz vectors (FP32): FP64 Rayleigh quotients, sort, store
-    TRY(store_eigvecs(ctx, n_ev, R, P->storage_precision, nullptr, nullptr));
+    // the head of B holds the n_ev wanted Ritz vectors (FP32): FP64 Rayleigh quotients, sort, store
+    TRY(store_eigvecs(ctx, n_ev, B, P->storage_precision, nullptr, nullptr));
     if (n_conv) *n_conv = conv;
     if (eps_out)
         for (int i = 0; i < n_ev; i++) eps_out[i] = ctx->eig.eps[i];

@@ -69,16 +69,9 @@ struct IngestOut {
     double2 *d;    // FP64 [mu][kind][fb][k][Vh] for this parity
     float4 *f;     // FP32 [mu][nk][k][Vh]
     float4 *f12;   // FP32 recon-12 long [mu][6][Vh] or null
-    uint2 *h;      // FP16 [mu][nk][k][Vh]
-    uint2 *h12;    // FP16 recon-12 long [mu][6][Vh] or null
     int nk;
 };
 
-__device__ __forceinline__ unsigned pack_half2(double re, double im)
-{
-    __half2 h = __floats2half2_rn(float(re), float(im));
-    return *reinterpret_cast<unsigned *>(&h);
-}
 
 // one thread per (output site cb, mu) of parity `par`
 __global__ void k_ingest(Geom g, int par, const double2 *__restrict__ fat, const double2 *__restrict__ lng,
@@ -131,22 +124,15 @@ __global__ void k_ingest(Geom g, int par, const double2 *__restrict__ fat, const
                 const double dev = fmax(su3_deviation(Sf), su3_deviation(Sb));
                 atomic_max_nonneg(max_dev, isfinite(dev) ? float(dev) : 1e30f);
                 float4 *q = o.f12 + size_t(mu * 6) * Vh + cb;
-                uint2 *qh = o.h12 + size_t(mu * 6) * Vh + cb;
 #pragma unroll
-                for (int k = 0; k < 6; k++) {
+                for (int k = 0; k < 6; k++)
                     __stcs(q + size_t(k) * Vh, make_float4(float(Sf[k].x), float(Sf[k].y), float(Sb[k].x), float(Sb[k].y)));
-                    __stcs(qh + size_t(k) * Vh, make_uint2(pack_half2(Sf[k].x, Sf[k].y), pack_half2(Sb[k].x, Sb[k].y)));
-                }
             } else {
                 float4 *q = o.f + size_t((mu * o.nk + kind) * 9) * Vh + cb;
-                uint2 *qh = o.h + size_t((mu * o.nk + kind) * 9) * Vh + cb;
 #pragma unroll
-                for (int k = 0; k < 9; k++) {
+                for (int k = 0; k < 9; k++)
                     __stcs(q + size_t(k) * Vh, make_float4(float(sf * Mf[k].x), float(sf * Mf[k].y),
                                                            float(sbk * Mb[k].x), float(sbk * Mb[k].y)));
-                    __stcs(qh + size_t(k) * Vh, make_uint2(pack_half2(sf * Mf[k].x, sf * Mf[k].y),
-                                                           pack_half2(sbk * Mb[k].x, sbk * Mb[k].y)));
-                }
             }
         }
     }
@@ -163,8 +149,7 @@ hisq_status ingest_links(hisq_ctx *ctx, const double *fat_dev, const double *lng
     HISQ_CUDA(cudaMemsetAsync(d_dev, 0, sizeof(float) + sizeof(int), ctx->stream));
     const int nk = recon == 12 ? 1 : 2;
     for (int par = 0; par < 2; par++) {
-        IngestOut o{ctx->links_d[par], ctx->links_f[par], recon == 12 ? ctx->links_f12[par] : nullptr, ctx->links_h[par],
-                    recon == 12 ? ctx->links_h12[par] : nullptr, nk};
+        IngestOut o{ctx->links_d[par], ctx->links_f[par], recon == 12 ? ctx->links_f12[par] : nullptr, nk};
         int grid = (4 * Vh + 255) / 256;
         if (grid > ctx->num_sms * 16) grid = ctx->num_sms * 16;
         ctx->launches++;
@@ -181,6 +166,44 @@ hisq_status ingest_links(hisq_ctx *ctx, const double *fat_dev, const double *lng
     HISQ_CUDA(cudaFreeAsync(d_dev, ctx->stream));
     if (max_unitarity_err) *max_unitarity_err = hdev;
     if (hbad) return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite link element");
+    return HISQ_OK;
+}
+
+} // namespace hisq
+
+namespace hisq {
+
+// FP16 gathered links: each FP32 (fwd, bwd) pair rounded to two half2 values
+__global__ void k_links_to_half(size_t n, const float4 *__restrict__ f, uint2 *__restrict__ h)
+{
+    for (size_t i = size_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += size_t(gridDim.x) * blockDim.x) {
+        const float4 a = f[i];
+        const __half2 x = __floats2half2_rn(a.x, a.y), y = __floats2half2_rn(a.z, a.w);
+        h[i] = make_uint2(*reinterpret_cast<const unsigned *>(&x), *reinterpret_cast<const unsigned *>(&y));
+    }
+}
+
+// the FP16 sloppy links exist only once an operator asks for them (they are
+// the rounding of the FP32 gathered links, so nothing else is needed)
+hisq_status ensure_half_links(hisq_ctx *ctx)
+{
+    if (ctx->links_h[0]) return HISQ_OK;
+    const size_t Vh = size_t(ctx->g.Vh);
+    const bool r12 = ctx->long_recon == 12;
+    const size_t nf = Vh * (r12 ? 4 : 8) * 9, n12 = Vh * 4 * 6;
+    for (int p = 0; p < 2; p++) {
+        ctx->links_h[p] = (uint2 *)dev_alloc(ctx, nf * 8);
+        if (r12) ctx->links_h12[p] = (uint2 *)dev_alloc(ctx, n12 * 8);
+        if (!ctx->links_h[p] || (r12 && !ctx->links_h12[p])) return HISQ_ERR_OOM;
+        ctx->launches++;
+        k_links_to_half<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(nf, ctx->links_f[p], ctx->links_h[p]);
+        HISQ_CUDA(cudaGetLastError());
+        if (r12) {
+            ctx->launches++;
+            k_links_to_half<<<ctx->num_sms * 8, 256, 0, ctx->stream>>>(n12, ctx->links_f12[p], ctx->links_h12[p]);
+            HISQ_CUDA(cudaGetLastError());
+        }
+    }
     return HISQ_OK;
 }
 

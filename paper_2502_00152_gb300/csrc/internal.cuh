@@ -812,6 +812,9 @@ hisq_status launch_convert(hisq_ctx *ctx, const void *in, int prec_in, void *out
 // out = a*x + b*y + c*D(in)  on output parity `out_parity`; x, y nullable,
 // all of precision `prec`, links of precision link_prec (64 or 32).
 // If norm_slot >= 0 the squared norm of out is reduced into scal->slot[norm_slot].
+// FP16 sloppy links, built from the FP32 gathered links on first use (ingest.cu)
+hisq_status ensure_half_links(hisq_ctx *ctx);
+
 hisq_status launch_dslash(hisq_ctx *ctx, int out_parity, int prec, int link_prec, const void *in,
                           void *out, double a, const void *x, double b, const void *y, double c,
                           int norm_slot);
@@ -840,9 +843,10 @@ hisq_status launch_defl_scale(hisq_ctx *ctx, int n, double *c_dev, const double 
 // FP32 field helpers for the eigensolver
 hisq_status launch_scale_f(hisq_ctx *ctx, double s, const void *in, void *out);
 hisq_status launch_random_f(hisq_ctx *ctx, unsigned long long seed, void *out);
-// basis rotation for the eigensolver: out_j = sum_i Y[i][j] in_i, real Y (k_in x k_out)
-hisq_status launch_rotate(hisq_ctx *ctx, int k_in, int k_out, const void *Vin, const double *Y_dev,
-                          void *Vout);
+// basis rotation for the eigensolver, in place: v_j <- sum_i Y[i][j] v_i for
+// j < k_out, real Y (k_in x k_out), through a tmp of k_out x chunk floats
+hisq_status launch_rotate_inplace(hisq_ctx *ctx, int k_in, int k_out, void *V, const double *Y_dev, float *tmp,
+                                  int chunk);
 
 // batched operator (mrhs.cu): active right-hand sides from ctx->bscal->idx
 hisq_status launch_mrhs_dslash_tt(hisq_ctx *ctx, int prec, int link_prec, void *p, void *tmp, int kact);

@@ -192,6 +192,14 @@ def gaussian_source(dims, seed: int, source: int) -> np.ndarray:
     return gaussian_field(dims, seed, STREAM_GAUSS_SOURCE, index0=source * 6 * volume(dims))
 
 
+def gaussian_colour_source(dims, seed: int, source: int, colour: int) -> np.ndarray:
+    """Colour-diluted Gaussian source: the colour-`colour` component of Gaussian
+    source `source` on every site, the other two colours zero."""
+    eta = np.zeros((volume(dims), 3), dtype=np.complex128)
+    eta[:, colour] = gaussian_source(dims, seed, source)[:, colour]
+    return eta
+
+
 def random_su3(n: int, seed: int, stream: int = STREAM_GAUGE_XFORM) -> np.ndarray:
     """n Haar-random SU(3) matrices: QR of a complex Gaussian matrix, with the
     phases of R's diagonal moved into Q (Mezzadri, Notices AMS 54 (2007) 592),
