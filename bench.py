@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="c2")
     ap.add_argument("--sloppy", type=int, default=16, help="sloppy colour-vector storage: 32 or 16")
-    ap.add_argument("--recon", type=int, default=12, help="long links: 18 reals or 12 (two rows + SU(3) row)")
+    ap.add_argument("--recon", type=int, default=12, help="long links: 18 reals, 12 (two rows + SU(3) row) or 8 (a2, a3, b1 and two phases)")
     ap.add_argument("--links", type=int, default=32, help="sloppy link storage: 32 or 16")
     ap.add_argument("--n-ev", type=int, default=None)
     ap.add_argument("--n-kr", type=int, default=None)
@@ -99,11 +99,9 @@ def measured_peak_hbm():
 
 
 def kernel_source_hash():
-    h = hashlib.sha256()
-    for rel in ("paper_2502_00152_gb300/csrc/dslash.cu", "paper_2502_00152_gb300/csrc/internal.cuh"):
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()[:16]
+    from paper_2502_00152_gb300.build import dslash_source_hash
+
+    return dslash_source_hash()
 
 
 def ncu_traffic(kernel_key: str, sites: int):
@@ -167,9 +165,9 @@ class Clocks:
 
 
 def link_bytes_per_site(recon: int, link_prec: int = 32) -> int:
-    # 8 fat + 8 long hop matrices of 18 reals (12 for the long ones with recon 12)
+    # 8 fat + 8 long hop matrices of 18 reals (12 or 8 for the long ones with recon 12 or 8)
     rb = link_prec // 8
-    return 8 * 18 * rb + 8 * (12 if recon == 12 else 18) * rb
+    return 8 * 18 * rb + 8 * recon * rb
 
 
 def spinor_bytes_per_site(prec: int) -> int:
@@ -211,7 +209,7 @@ def run_ours(a):
     t_links = time.time() - t0
     stream = torch.cuda.current_stream()
     ctx = H.hisq_create(dims, t_antiperiodic=True, device=local, cuda_stream=stream.cuda_stream)
-    H.hisq_load_links(ctx, fat, lng, long_recon=a.recon, long_scale=I.C3_NAIK if a.recon == 12 else 1.0)
+    H.hisq_load_links(ctx, fat, lng, long_recon=a.recon, long_scale=I.C3_NAIK if a.recon != 18 else 1.0)
     H.hisq_set_mass(ctx, m)
 
     # setup: eigensolve (excluded from the solve time, reported)
@@ -497,7 +495,7 @@ def run_learned(a):
     V = I.volume(dims)
     fat, lng = I.hisq_links(dims, cfg["seed"], cfg["eps"])
     ctx = H.hisq_create(dims, True, 0, torch.cuda.current_stream().cuda_stream)
-    H.hisq_load_links(ctx, fat, lng, long_recon=a.recon, long_scale=I.C3_NAIK if a.recon == 12 else 1.0)
+    H.hisq_load_links(ctx, fat, lng, long_recon=a.recon, long_scale=I.C3_NAIK if a.recon != 18 else 1.0)
     H.hisq_set_mass(ctx, m)
     del fat, lng
     t0 = time.time()
@@ -535,20 +533,24 @@ def run_learned(a):
     t_train = time.time() - t0
     # held-out right-hand sides
     etas = np.stack([I.gaussian_source(dims, 3, 100000 + q) for q in range(24)])
+    eta_dev = torch.from_numpy(etas).cuda()
+    psi_dev = torch.zeros_like(eta_dev)
     res = {}
     for name, p, use_net in (("zero", H.hisq_default_solve_params(deflate=0, batch=1, precision_sloppy=a.sloppy), False),
                              ("deflated", prm, False),
                              ("deflated+learned", H.hisq_default_solve_params(deflate=1, batch=1, guess=1,
                                                                               precision_sloppy=a.sloppy), True)):
-        H.hisq_solve(ctx, etas[:3], p, guess=np.zeros_like(etas[:3]) if use_net else None)  # warm-up
+        psi_dev.zero_()
+        H.hisq_solve_device(ctx, eta_dev[:3].contiguous(), psi_dev[:3].contiguous(), 3, p)  # warm-up
         torch.cuda.synchronize()
         t0 = time.time()
-        guess = None
-        if use_net:
+        psi_dev.zero_()
+        if use_net:  # the guess is produced on the device and read there by the solve
             with torch.no_grad():
-                xin = torch.from_numpy(etas.astype(np.complex64)).cuda()
-                guess = torch.cat([net(xin[i:i + 3]) for i in range(0, 24, 3)]).cpu().numpy().astype(np.complex128)
-        psi, st, s = H.hisq_solve(ctx, etas, p, guess=guess)
+                xin = eta_dev.to(torch.complex64)
+                for i in range(0, 24, 3):
+                    psi_dev[i:i + 3] = net(xin[i:i + 3]).to(torch.complex128)
+        st, s = H.hisq_solve_device(ctx, eta_dev, psi_dev, 24, p)
         torch.cuda.synchronize()
         dt = (time.time() - t0) * 1e3 / 24
         res[name] = dict(ms_per_rhs=round(dt, 3), iterations=float(np.mean([x["iterations"] for x in st])),
@@ -596,7 +598,7 @@ def run_sweep(a):
     fat, lng = I.hisq_links(dims, cfg["seed"], cfg["eps"])
     stream = torch.cuda.current_stream()
     ctx = H.hisq_create(dims, t_antiperiodic=True, device=0, cuda_stream=stream.cuda_stream)
-    H.hisq_load_links(ctx, fat, lng, long_recon=a.recon, long_scale=I.C3_NAIK if a.recon == 12 else 1.0)
+    H.hisq_load_links(ctx, fat, lng, long_recon=a.recon, long_scale=I.C3_NAIK if a.recon != 18 else 1.0)
     del fat, lng
     H.hisq_set_mass(ctx, m0)
     n_ev = a.n_ev if a.n_ev is not None else 256

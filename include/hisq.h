@@ -147,9 +147,12 @@ const char *hisq_status_string(hisq_status s);
 /* Load the fat (one-hop) and long (three-hop) links, FP64 host layout above,
  * coefficients folded in.  long_recon = 18 stores all 18 reals of the long links;
  * 12 stores two rows of long/long_scale (which must then be SU(3) to 1e-6;
- * otherwise HISQ_ERR_INVALID_ARG) and rebuilds the third row on the fly.  The
- * library folds staggered phases, boundary signs and the backward adjoints into
- * its own device copies (FP64, FP32 and FP16).  Non-finite input: HISQ_ERR_NUMERICAL. */
+ * otherwise HISQ_ERR_INVALID_ARG) and rebuilds the third row on the fly; 8
+ * stores (a2, a3, b1, arg a1, arg c1) of the same SU(3) factor and rebuilds the
+ * rest from unitarity (FP32 sloppy operator only; FP16 links need 18 or 12).  The
+ * FP64 copy always holds all 18 reals.  The library folds staggered phases,
+ * boundary signs and the backward adjoints into its own device copies (FP64,
+ * FP32; FP16 built on first use).  Non-finite input: HISQ_ERR_NUMERICAL. */
 hisq_status hisq_load_links(hisq_ctx *ctx, const double *fat, const double *lng, int long_recon,
                             double long_scale);
 
@@ -250,6 +253,13 @@ hisq_status hisq_load_eigvecs(hisq_ctx *ctx, const char *path);
  * Events are recorded on the context's stream around the two Dslash kernels of
  * every iteration; the sums are returned in hisq_solve_stats. */
 hisq_status hisq_set_profiling(hisq_ctx *ctx, int on);
+
+/* Failure injection on the host (tests of the error paths; the paper has no
+ * counterpart): after `after` further successful device allocations by this
+ * context, every allocation fails as if the device were out of memory, so the
+ * call in progress returns HISQ_ERR_OOM with a message.  after < 0 switches the
+ * injection off; the context stays usable.  Nothing is done on the device. */
+hisq_status hisq_inject_alloc_failure(hisq_ctx *ctx, int after);
 
 /* ---- learned initial guess: gauge-covariant parallel-transport layers.
  * The paper has no learned part; these entry points serve a small network that

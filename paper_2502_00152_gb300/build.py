@@ -51,6 +51,16 @@ def _stamp(paths) -> str:
     return h.hexdigest()
 
 
+def dslash_source_hash() -> str:
+    """Hash of the sources that determine the single-RHS Dslash kernels; a
+    stored ncu traffic figure is valid only for the hash it was taken on."""
+    h = hashlib.sha256()
+    for name in ("dslash.cu", "internal.cuh"):
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     srcs = _sources()
     stamp = _stamp(srcs + _headers())

@@ -66,6 +66,11 @@ void *dev_alloc(hisq_ctx *c, size_t bytes)
 {
     void *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (c->alloc_fail_after == 0) {
+        set_err(c, HISQ_ERR_OOM, "allocation of %zu bytes refused (injected failure)", bytes);
+        return nullptr;
+    }
+    if (c->alloc_fail_after > 0) c->alloc_fail_after--;
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         set_err(c, HISQ_ERR_OOM, "cudaMalloc of %zu bytes failed", bytes);
@@ -271,8 +276,9 @@ hisq_status hisq_load_links(hisq_ctx *ctx, const double *fat, const double *lng,
 {
     if (!ctx) return HISQ_ERR_INVALID_ARG;
     if (!fat || !lng) return set_err(ctx, HISQ_ERR_INVALID_ARG, "null link array");
-    if (long_recon != 18 && long_recon != 12) return set_err(ctx, HISQ_ERR_INVALID_ARG, "long_recon must be 18 or 12");
-    if (long_recon == 12 && (!(std::fabs(long_scale) > 0) || !std::isfinite(long_scale)))
+    if (long_recon != 18 && long_recon != 12 && long_recon != 8)
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "long_recon must be 18, 12 or 8");
+    if (long_recon != 18 && (!(std::fabs(long_scale) > 0) || !std::isfinite(long_scale)))
         return set_err(ctx, HISQ_ERR_INVALID_ARG, "long_scale must be finite and non-zero");
     HISQ_CUDA(cudaSetDevice(ctx->device));
     const int Vh = ctx->g.Vh;
@@ -281,11 +287,11 @@ hisq_status hisq_load_links(hisq_ctx *ctx, const double *fat, const double *lng,
     for (int p = 0; p < 2; p++) {
         dev_free(ctx, ctx->links_d[p], size_t(Vh) * 16 * 9 * 16);
         ctx->links_d[p] = nullptr;
-        dev_free(ctx, ctx->links_f[p], size_t(Vh) * (ctx->long_recon == 12 ? 4 : 8) * 9 * 16);
+        dev_free(ctx, ctx->links_f[p], size_t(Vh) * (ctx->long_recon == 18 ? 8 : 4) * 9 * 16);
         ctx->links_f[p] = nullptr;
-        dev_free(ctx, ctx->links_f12[p], size_t(Vh) * 4 * 6 * 16);
+        dev_free(ctx, ctx->links_f12[p], size_t(Vh) * long_f32_bytes_per_site(ctx->long_recon));
         ctx->links_f12[p] = nullptr;
-        dev_free(ctx, ctx->links_h[p], size_t(Vh) * (ctx->long_recon == 12 ? 4 : 8) * 9 * 8);
+        dev_free(ctx, ctx->links_h[p], size_t(Vh) * (ctx->long_recon == 18 ? 8 : 4) * 9 * 8);
         ctx->links_h[p] = nullptr;
         dev_free(ctx, ctx->links_h12[p], size_t(Vh) * 4 * 6 * 8);
         ctx->links_h12[p] = nullptr;
@@ -293,13 +299,13 @@ hisq_status hisq_load_links(hisq_ctx *ctx, const double *fat, const double *lng,
     ctx->links_loaded = false;
     for (int p = 0; p < 2; p++) {
         ctx->links_d[p] = (double2 *)dev_alloc(ctx, size_t(Vh) * 16 * 9 * 16);
-        ctx->links_f[p] = (float4 *)dev_alloc(ctx, size_t(Vh) * (long_recon == 12 ? 4 : 8) * 9 * 16);
-        if (long_recon == 12) ctx->links_f12[p] = (float4 *)dev_alloc(ctx, size_t(Vh) * 4 * 6 * 16);
-        if (!ctx->links_d[p] || !ctx->links_f[p] || (long_recon == 12 && !ctx->links_f12[p])) return HISQ_ERR_OOM;
+        ctx->links_f[p] = (float4 *)dev_alloc(ctx, size_t(Vh) * (long_recon == 18 ? 8 : 4) * 9 * 16);
+        if (long_recon != 18) ctx->links_f12[p] = (float4 *)dev_alloc(ctx, size_t(Vh) * long_f32_bytes_per_site(long_recon));
+        if (!ctx->links_d[p] || !ctx->links_f[p] || (long_recon != 18 && !ctx->links_f12[p])) return HISQ_ERR_OOM;
         // FP16 links are built from the FP32 ones on first use (ensure_half_links)
     }
     ctx->long_recon = long_recon;
-    ctx->long_scale = long_recon == 12 ? long_scale : 1.0;
+    ctx->long_scale = long_recon != 18 ? long_scale : 1.0;
     double *stage = nullptr;
     HISQ_CUDA(cudaMalloc(&stage, 2 * nlink));
     cudaError_t e1 = cudaMemcpyAsync(stage, fat, nlink, cudaMemcpyHostToDevice, ctx->stream);
@@ -311,7 +317,7 @@ hisq_status hisq_load_links(hisq_ctx *ctx, const double *fat, const double *lng,
     cudaStreamSynchronize(ctx->stream);
     cudaFree(stage);
     if (st != HISQ_OK) return st;
-    if (long_recon == 12 && !(dev <= 1e-6))
+    if (long_recon != 18 && !(dev <= 1e-6))
         return set_err(ctx, HISQ_ERR_INVALID_ARG, "long links / long_scale are not SU(3) (deviation %.3g)", dev);
     ctx->links_loaded = true;
     return HISQ_OK;
@@ -375,6 +381,13 @@ hisq_status hisq_apply_dslash(hisq_ctx *ctx, int out_parity, int precision, int 
     HISQ_CUDA(cudaMemsetAsync(full, 0, size_t(ctx->g.V) * 48, ctx->stream));
     TRY(launch_scatter_parity(ctx, b, precision, out_parity, full));
     return download_full(ctx, full, out);
+}
+
+hisq_status hisq_inject_alloc_failure(hisq_ctx *ctx, int after)
+{
+    if (!ctx) return HISQ_ERR_INVALID_ARG;
+    ctx->alloc_fail_after = after < 0 ? -1 : after;
+    return HISQ_OK;
 }
 
 hisq_status hisq_apply_normal_op(hisq_ctx *ctx, int precision, int link_precision, const double *in, double *out)

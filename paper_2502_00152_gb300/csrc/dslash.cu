@@ -230,8 +230,8 @@ static hisq_status run_any(hisq_ctx *ctx, int par, int link_prec, const S &in, c
 {
     typedef typename S::real R;
     const int Vh = ctx->g.Vh;
-    const bool r12 = ctx->long_recon == 12;
-    const int nk = r12 ? 1 : 2;
+    const bool r12 = ctx->long_recon == 12, r8 = ctx->long_recon == 8;
+    const int nk = (r12 || r8) ? 1 : 2;
     if (link_prec == 64) {
         if constexpr (sizeof(R) == 8)
             return run_dslash<S, LinksD, LinksF12, false>(ctx, par, LinksD{ctx->links_d[par], Vh}, LinksF12{nullptr, Vh},
@@ -242,6 +242,7 @@ static hisq_status run_any(hisq_ctx *ctx, int par, int link_prec, const S &in, c
         if (link_prec == 32) {
             LinksFv L{ctx->links_f[par], Vh, nk};
             if (r12) return run_dslash<S, LinksFv, LinksF12, true>(ctx, par, L, LinksF12{ctx->links_f12[par], Vh}, in, epi, ra, dored);
+            if (r8) return run_dslash<S, LinksFv, LinksF8, true>(ctx, par, L, LinksF8{ctx->links_f12[par], Vh}, in, epi, ra, dored);
             return run_dslash<S, LinksFv, LinksF12, false>(ctx, par, L, LinksF12{nullptr, Vh}, in, epi, ra, dored);
         }
         if (link_prec == 16) {

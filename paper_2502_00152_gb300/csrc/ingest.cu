@@ -68,7 +68,7 @@ __device__ __forceinline__ void atomic_max_nonneg(float *addr, float v)
 struct IngestOut {
     double2 *d;    // FP64 [mu][kind][fb][k][Vh] for this parity
     float4 *f;     // FP32 [mu][nk][k][Vh]
-    float4 *f12;   // FP32 recon-12 long [mu][6][Vh] or null
+    float4 *f12;   // FP32 compressed long: recon 12 [mu][6][Vh], recon 8 [mu][4][Vh], or null
     int nk;
 };
 
@@ -113,7 +113,7 @@ __global__ void k_ingest(Geom g, int par, const double2 *__restrict__ fat, const
                 qd[size_t(k) * Vh] = make_double2(sf * Mf[k].x, sf * Mf[k].y);
                 qd[size_t(9 + k) * Vh] = make_double2(sbk * Mb[k].x, sbk * Mb[k].y);
             }
-            if (kind == 1 && recon == 12) {
+            if (kind == 1 && recon != 18) {
                 // SU(3) factor, rows 0 and 1
                 double2 Sf[9], Sb[9];
 #pragma unroll
@@ -123,10 +123,22 @@ __global__ void k_ingest(Geom g, int par, const double2 *__restrict__ fat, const
                 }
                 const double dev = fmax(su3_deviation(Sf), su3_deviation(Sb));
                 atomic_max_nonneg(max_dev, isfinite(dev) ? float(dev) : 1e30f);
-                float4 *q = o.f12 + size_t(mu * 6) * Vh + cb;
+                if (recon == 12) {
+                    float4 *q = o.f12 + size_t(mu * 6) * Vh + cb;
 #pragma unroll
-                for (int k = 0; k < 6; k++)
-                    __stcs(q + size_t(k) * Vh, make_float4(float(Sf[k].x), float(Sf[k].y), float(Sb[k].x), float(Sb[k].y)));
+                    for (int k = 0; k < 6; k++)
+                        __stcs(q + size_t(k) * Vh,
+                               make_float4(float(Sf[k].x), float(Sf[k].y), float(Sb[k].x), float(Sb[k].y)));
+                } else { // recon 8: (a2, a3), (b1, arg a1, arg c1) of fwd, then of bwd
+                    float4 *q = o.f12 + size_t(mu * 4) * Vh + cb;
+                    const double2 *S2[2] = {Sf, Sb};
+                    for (int fb = 0; fb < 2; fb++) {
+                        const double2 *S = S2[fb];
+                        __stcs(q + size_t(2 * fb) * Vh, make_float4(float(S[1].x), float(S[1].y), float(S[2].x), float(S[2].y)));
+                        __stcs(q + size_t(2 * fb + 1) * Vh, make_float4(float(S[3].x), float(S[3].y), float(atan2(S[0].y, S[0].x)),
+                                                                        float(atan2(S[6].y, S[6].x))));
+                    }
+                }
             } else {
                 float4 *q = o.f + size_t((mu * o.nk + kind) * 9) * Vh + cb;
 #pragma unroll
@@ -147,9 +159,9 @@ hisq_status ingest_links(hisq_ctx *ctx, const double *fat_dev, const double *lng
     HISQ_CUDA(cudaMallocAsync((void **)&d_dev, sizeof(float) + sizeof(int), ctx->stream));
     d_bad = reinterpret_cast<int *>(d_dev + 1);
     HISQ_CUDA(cudaMemsetAsync(d_dev, 0, sizeof(float) + sizeof(int), ctx->stream));
-    const int nk = recon == 12 ? 1 : 2;
+    const int nk = recon == 18 ? 2 : 1;
     for (int par = 0; par < 2; par++) {
-        IngestOut o{ctx->links_d[par], ctx->links_f[par], recon == 12 ? ctx->links_f12[par] : nullptr, nk};
+        IngestOut o{ctx->links_d[par], ctx->links_f[par], recon != 18 ? ctx->links_f12[par] : nullptr, nk};
         int grid = (4 * Vh + 255) / 256;
         if (grid > ctx->num_sms * 16) grid = ctx->num_sms * 16;
         ctx->launches++;
@@ -188,6 +200,7 @@ __global__ void k_links_to_half(size_t n, const float4 *__restrict__ f, uint2 *_
 hisq_status ensure_half_links(hisq_ctx *ctx)
 {
     if (ctx->links_h[0]) return HISQ_OK;
+    if (ctx->long_recon == 8) return set_err(ctx, HISQ_ERR_INVALID_ARG, "FP16 links need long_recon 18 or 12");
     const size_t Vh = size_t(ctx->g.Vh);
     const bool r12 = ctx->long_recon == 12;
     const size_t nf = Vh * (r12 ? 4 : 8) * 9, n12 = Vh * 4 * 6;

@@ -330,6 +330,9 @@ __device__ __forceinline__ CVec<To> cvt(const CVec<From> &v)
 // FP32 long links with recon 12: float4 [p][mu][k=0..5][Vh] holding rows 0,1
 //   of the SU(3) factor S of fwd and bwd; W = sign * long_scale * S, with
 //   sign = +-eta_mu(x) * (boundary sign) recomputed from the coordinates.
+// FP32 long links with recon 8: float4 [p][mu][q=0..3][Vh]: q = 0, 1 for fwd,
+//   2, 3 for bwd, each pair (a2, a3) and (b1, arg a1, arg c1) of the SU(3)
+//   factor (a = row 0, b = row 1, c = row 2); the rest follows from unitarity.
 // FP16 (recon 18): uint2 [p][mu][kind][k=0..8][Vh], uint2 = (fwd_k, bwd_k) as
 //   two half2; FP16 long links with recon 12: uint2 [p][mu][k=0..5][Vh].
 struct LinksD {
@@ -387,6 +390,68 @@ struct LinksF12 { // long links only
         su3_third_row(b);
     }
 };
+
+// SU(3) matrix from 8 reals: row 0 = (a1, a2, a3), column 0 = (a1, b1, c1)
+// with |a1|, |c1| from the unit norms of row 0 and column 0 and the phases of
+// a1, c1 stored; the four remaining entries follow from U = conj(cofactors)
+// (c = conj(a x b), b = conj(c x a)) solved for b2, b3, c2, c3, each over
+// N = |a2|^2 + |a3|^2 = 1 - |a1|^2.
+__device__ __forceinline__ void su3_from8(const float4 p0, const float4 p1, CMat<float> &W)
+{
+    const float a2r = p0.x, a2i = p0.y, a3r = p0.z, a3i = p0.w, b1r = p1.x, b1i = p1.y;
+    const float N = a2r * a2r + a2i * a2i + a3r * a3r + a3i * a3i;
+    const float ma1 = sqrtf(fmaxf(0.f, 1.f - N));
+    const float mc1 = sqrtf(fmaxf(0.f, N - (b1r * b1r + b1i * b1i)));
+    float sa, ca, sc, cc;
+    sincosf(p1.z, &sa, &ca);
+    sincosf(p1.w, &sc, &cc);
+    const float a1r = ma1 * ca, a1i = ma1 * sa, c1r = mc1 * cc, c1i = mc1 * sc;
+    const float iN = 1.f / N;
+    // complex helpers on (re, im) pairs
+    auto mul = [](float xr, float xi, float yr, float yi, float &zr, float &zi) {
+        zr = xr * yr - xi * yi;
+        zi = xr * yi + xi * yr;
+    };
+    float tr, ti, ur, ui;
+    // b2 = -(conj(a1) a2 b1 + conj(a3) conj(c1)) / N
+    mul(a1r, -a1i, a2r, a2i, tr, ti);
+    mul(tr, ti, b1r, b1i, tr, ti);
+    mul(a3r, -a3i, c1r, -c1i, ur, ui);
+    const float b2r = -(tr + ur) * iN, b2i = -(ti + ui) * iN;
+    // b3 = (conj(a2) conj(c1) - conj(a1) a3 b1) / N
+    mul(a2r, -a2i, c1r, -c1i, ur, ui);
+    mul(a1r, -a1i, a3r, a3i, tr, ti);
+    mul(tr, ti, b1r, b1i, tr, ti);
+    const float b3r = (ur - tr) * iN, b3i = (ui - ti) * iN;
+    // c2 = (conj(a3) conj(b1) - conj(a1) a2 c1) / N
+    mul(a3r, -a3i, b1r, -b1i, ur, ui);
+    mul(a1r, -a1i, a2r, a2i, tr, ti);
+    mul(tr, ti, c1r, c1i, tr, ti);
+    const float c2r = (ur - tr) * iN, c2i = (ui - ti) * iN;
+    // c3 = -(conj(a1) a3 c1 + conj(a2) conj(b1)) / N
+    mul(a1r, -a1i, a3r, a3i, tr, ti);
+    mul(tr, ti, c1r, c1i, tr, ti);
+    mul(a2r, -a2i, b1r, -b1i, ur, ui);
+    const float c3r = -(tr + ur) * iN, c3i = -(ti + ui) * iN;
+    W.re[0] = a1r; W.im[0] = a1i; W.re[1] = a2r; W.im[1] = a2i; W.re[2] = a3r; W.im[2] = a3i;
+    W.re[3] = b1r; W.im[3] = b1i; W.re[4] = b2r; W.im[4] = b2i; W.re[5] = b3r; W.im[5] = b3i;
+    W.re[6] = c1r; W.im[6] = c1i; W.re[7] = c2r; W.im[7] = c2i; W.re[8] = c3r; W.im[8] = c3i;
+}
+
+struct LinksF8 { // long links only, 8 reals per SU(3) factor
+    const float4 *base; // parity offset applied
+    int Vh;
+    __device__ __forceinline__ void load(int mu, int i, CMat<float> &f, CMat<float> &b) const
+    {
+        const float4 *q = base + size_t(mu * 4) * Vh + i;
+        const float4 f0 = __ldcs(q), f1 = __ldcs(q + Vh), b0 = __ldcs(q + 2 * size_t(Vh)), b1 = __ldcs(q + 3 * size_t(Vh));
+        su3_from8(f0, f1, f);
+        su3_from8(b0, b1, b);
+    }
+};
+
+// floats of compressed FP32 long links per output site and parity (0: none)
+inline size_t long_f32_bytes_per_site(int recon) { return recon == 12 ? 4 * 6 * 16 : (recon == 8 ? 4 * 4 * 16 : 0); }
 
 // ------------------------------------------------------ device scalars
 // Scalars of the CG recurrences live on the device so that consecutive kernels
@@ -618,6 +683,9 @@ struct hisq_ctx {
     double *bmonitor_h = nullptr; // host-mapped
     double *bmonitor_d = nullptr;
     int bmonitor_len = 4096;
+
+    // host-side failure injection: allocations left before they fail (-1: off)
+    long long alloc_fail_after = -1;
 
     // launch shapes chosen by the autotuner, by problem key
     std::map<unsigned long long, int> tuned;

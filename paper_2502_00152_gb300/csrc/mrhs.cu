@@ -354,7 +354,7 @@ static hisq_status run_mrhs_r(hisq_ctx *ctx, int par, const BatchF<S> &in, const
 {
     const int Vh = ctx->g.Vh;
     const int threads = 32 * tl.nch * tl.nsg;
-    LinksFvB L{ctx->links_f[par], Vh, ctx->long_recon == 12 ? 1 : 2};
+    LinksFvB L{ctx->links_f[par], Vh, ctx->long_recon == 18 ? 2 : 1};
     auto launch = [&](auto kern, auto L12) -> hisq_status {
         const int grid = grid_for(ctx, long(Vh), 32 * tl.nsg, mrhs_blocks_per_sm(kern, threads));
         kern<<<grid, threads, 0, ctx->stream>>>(ctx->g, par, L, L12, float(ctx->long_scale), in, ctx->bscal, tl, epi,
@@ -365,6 +365,8 @@ static hisq_status run_mrhs_r(hisq_ctx *ctx, int par, const BatchF<S> &in, const
     };
     if (ctx->long_recon == 12)
         return launch(k_dslash_mrhs<R, S, LinksFvB, LinksF12, true, Epi>, LinksF12{ctx->links_f12[par], Vh});
+    if (ctx->long_recon == 8)
+        return launch(k_dslash_mrhs<R, S, LinksFvB, LinksF8, true, Epi>, LinksF8{ctx->links_f12[par], Vh});
     return launch(k_dslash_mrhs<R, S, LinksFvB, LinksF12, false, Epi>, LinksF12{nullptr, Vh});
 }
 

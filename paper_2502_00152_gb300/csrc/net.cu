@@ -260,7 +260,7 @@ hisq_status hisq_net_layer(hisq_ctx *ctx, int cin, int cout, const float *w_dev,
     }
     const int nblk = (ctx->g.V + kNetSites - 1) / kNetSites;
     const int grid = std::min(nblk, ctx->num_sms * 4);
-    const int nk = ctx->long_recon == 12 ? 1 : 2;
+    const int nk = ctx->long_recon == 18 ? 2 : 1;
     ctx->launches++;
     k_net_layer<<<grid, 256, smem, ctx->stream>>>(ctx->g, ctx->links_f[0], ctx->links_f[1], nk, (const float2 *)w_dev,
                                                   cin, cout, adjoint, w_bf16, (const float2 *)in_dev, (float2 *)out_dev);
@@ -286,7 +286,7 @@ hisq_status hisq_net_wgrad(hisq_ctx *ctx, int cin, int cout, const float *in_dev
     const int ntrip = cin * cout * kNetHops;
     double2 *part = (double2 *)get_buf(ctx, BUF_NET_PART, sizeof(double2) * size_t(grid) * ntrip);
     if (!part) return HISQ_ERR_OOM;
-    const int nk = ctx->long_recon == 12 ? 1 : 2;
+    const int nk = ctx->long_recon == 18 ? 2 : 1;
     ctx->launches += 2;
     k_net_wgrad<<<grid, 256, smem, ctx->stream>>>(ctx->g, ctx->links_f[0], ctx->links_f[1], nk, cin, cout,
                                                   (const float2 *)in_dev, (const float2 *)gout_dev, part);

@@ -435,9 +435,9 @@ hisq_status hisq_solve(hisq_ctx *ctx, const double *eta, double *psi, int nrhs, 
             if (s != HISQ_OK) worst = s;
         }
         if (worst != HISQ_OK) {
-        const std::string why = ctx->err;
-        set_err(ctx, worst, "at least one right-hand side did not converge (%s)", why.c_str());
-    }
+            const std::string why = ctx->err;
+            set_err(ctx, worst, "at least one right-hand side did not converge (%s)", why.c_str());
+        }
         return worst;
     }
     double *de = (double *)get_buf(ctx, BUF_ETA_FULL, bytes);
@@ -489,9 +489,9 @@ hisq_status hisq_solve_device(hisq_ctx *ctx, const double *eta_dev, double *psi_
             if (s != HISQ_OK) worst = s;
         }
         if (worst != HISQ_OK) {
-        const std::string why = ctx->err;
-        set_err(ctx, worst, "at least one right-hand side did not converge (%s)", why.c_str());
-    }
+            const std::string why = ctx->err;
+            set_err(ctx, worst, "at least one right-hand side did not converge (%s)", why.c_str());
+        }
         return worst;
     }
     for (int k = 0; k < nrhs; k++) {

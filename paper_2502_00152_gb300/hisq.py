@@ -96,6 +96,7 @@ _PROTOS = [
     ("hisq_save_eigvecs", ctypes.c_int, [_CTX, ctypes.c_char_p]),
     ("hisq_load_eigvecs", ctypes.c_int, [_CTX, ctypes.c_char_p]),
     ("hisq_set_profiling", ctypes.c_int, [_CTX, ctypes.c_int]),
+    ("hisq_inject_alloc_failure", ctypes.c_int, [_CTX, ctypes.c_int]),
     ("hisq_device_bytes", ctypes.c_size_t, [_CTX]),
     ("hisq_kernel_launches", ctypes.c_ulonglong, [_CTX]),
 ]
@@ -321,6 +322,12 @@ def hisq_save_eigvecs(ctx: Context, path: str) -> None:
 
 def hisq_load_eigvecs(ctx: Context, path: str) -> None:
     _check(ctx.handle, load_library().hisq_load_eigvecs(ctx.handle, path.encode()))
+
+
+def hisq_inject_alloc_failure(ctx: Context, after: int) -> None:
+    """Host-side failure injection: device allocations fail after `after` more
+    (after < 0 switches it off)."""
+    _check(ctx.handle, load_library().hisq_inject_alloc_failure(ctx.handle, int(after)))
 
 
 def hisq_set_profiling(ctx: Context, on: bool = True) -> None:

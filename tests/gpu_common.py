@@ -10,7 +10,7 @@ def make(dims, seed=3, eps=0.4, antip=True, recon=18, mass=None):
     fat, lng = I.hisq_links(dims, seed, eps)
     o = Oracle(dims, fat, lng, t_antiperiodic=antip)
     ctx = H.hisq_create(dims, t_antiperiodic=antip, device=0)
-    H.hisq_load_links(ctx, fat, lng, long_recon=recon, long_scale=I.C3_NAIK if recon == 12 else 1.0)
+    H.hisq_load_links(ctx, fat, lng, long_recon=recon, long_scale=I.C3_NAIK if recon != 18 else 1.0)
     if mass is not None:
         H.hisq_set_mass(ctx, mass)
     return ctx, o

@@ -55,6 +55,32 @@ def test_dslash_long_recon12(dims):
         ctx.close()
 
 
+@pytest.mark.parametrize("dims,eps", [((6, 6, 6, 6), 0.4), ((4, 6, 4, 10), 0.3), ((8, 8, 8, 12), 0.1)])
+def test_dslash_long_recon8(dims, eps):
+    """8-real long links: (a2, a3, b1, arg a1, arg c1) of the SU(3) factor, the
+    rest rebuilt from unitarity with FP32 arithmetic.  The rebuilt entries
+    carry the FP32 rounding amplified by 1/N, N = |a2|^2 + |a3|^2 (the links
+    here are near the identity, N ~ 0.05 at eps 0.1), hence 1e-5 for FP32
+    vectors; FP16 storage dominates otherwise."""
+    fat, lng = I.hisq_links(dims, 3, eps)
+    from oracle.oracle import Oracle
+
+    o = Oracle(dims, fat, lng)
+    ctx = H.hisq_create(dims)
+    try:
+        H.hisq_load_links(ctx, fat, lng, long_recon=8, long_scale=I.C3_NAIK)
+        src = I.gaussian_field(dims, 18)
+        for par in (0, 1):
+            ref = dslash_ref(o, dims, src, par)
+            assert rel(H.hisq_apply_dslash(ctx, par, 64, src, link_precision=64), ref) <= TOL[64]
+            assert rel(H.hisq_apply_dslash(ctx, par, 32, src, link_precision=32), ref) <= 1e-5
+            assert rel(H.hisq_apply_dslash(ctx, par, 16, src, link_precision=32), ref) <= TOL[16]
+        with pytest.raises(H.HisqError):  # FP16 links are not offered with 8-real long links
+            H.hisq_apply_dslash(ctx, 0, 16, src, link_precision=16)
+    finally:
+        ctx.close()
+
+
 def test_recon12_rejects_non_su3_links():
     dims = (4, 4, 4, 6)
     fat, lng = I.hisq_links(dims, 1, 0.3)

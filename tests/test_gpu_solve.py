@@ -82,6 +82,22 @@ def test_z2_wall_source_and_recon12():
         ctx.close()
 
 
+def test_recon8_solves_single_and_batched():
+    dims = (6, 6, 6, 8)
+    m = 0.02
+    ctx, o = make(dims, seed=5, eps=0.3, mass=m, recon=8)
+    try:
+        etas = np.stack([I.z2_wall_source(dims, 7, 3, c) for c in range(3)])
+        psi, st, status = H.hisq_solve(ctx, etas[0], H.hisq_default_solve_params(precision_sloppy=16))
+        assert status == H.HISQ_OK and o.full_residual(m, psi, etas[0]) <= 1e-10
+        psi, st, status = H.hisq_solve(ctx, etas, H.hisq_default_solve_params(precision_sloppy=16, batch=1))
+        assert status == H.HISQ_OK
+        for j in range(3):
+            assert o.full_residual(m, psi[j], etas[j]) <= 1e-10
+    finally:
+        ctx.close()
+
+
 def test_zero_source():
     dims = (4, 4, 4, 4)
     ctx, o = make(dims, mass=0.1)
@@ -158,5 +174,27 @@ def test_fp16_links_stagnation_is_reported():
             assert status == H.HISQ_ERR_NOT_CONVERGED
             assert st[0]["iterations"] < 20000
             assert "stagnation" in H.hisq_last_error(ctx)
+    finally:
+        ctx.close()
+
+
+def test_injected_allocation_failure_is_reported_and_recovered():
+    """Host-side fault injection: allocations refused mid-solve give
+    HISQ_ERR_OOM with a message; with the injection off the same context
+    solves to the tolerance."""
+    dims = (6, 6, 6, 8)
+    ctx, o = make(dims, seed=5, eps=0.3, mass=0.05)
+    try:
+        eta = I.gaussian_source(dims, 3, 0)
+        H.hisq_inject_alloc_failure(ctx, 0)
+        with pytest.raises(H.HisqError) as ei:
+            H.hisq_solve(ctx, eta, H.hisq_default_solve_params())
+        assert "injected" in str(ei.value)
+        H.hisq_inject_alloc_failure(ctx, 2)  # fails part-way through buffer set-up
+        with pytest.raises(H.HisqError):
+            H.hisq_solve(ctx, eta, H.hisq_default_solve_params())
+        H.hisq_inject_alloc_failure(ctx, -1)
+        psi, st, status = H.hisq_solve(ctx, eta, H.hisq_default_solve_params())
+        assert status == H.HISQ_OK and o.full_residual(0.05, psi, eta) <= 1e-10
     finally:
         ctx.close()
