@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--learned-pairs", type=int, default=512)
     ap.add_argument("--learned-epochs", type=int, default=30)
     ap.add_argument("--learned-lr", type=float, default=2e-3)
-    ap.add_argument("--sweep", choices=["delta_tr", "mass"], default=None,
+    ap.add_argument("--sweep", choices=["delta_tr", "mass", "cheby"], default=None,
                     help="precision/re-deflation sweep (Fig. 2 analogue) or iterations vs mass (Fig. 1 analogue) "
                          "on the 32^3x64 lattice; prints one JSON line per table")
     ap.add_argument("--rhs-per-step", type=int, default=None,
@@ -584,7 +584,8 @@ def run_sweep(a):
     256 eigenpairs; delta_tr = 0 switches re-deflation off (Fig. 2 analogue).
     mass: plain and deflated CG iterations and time per RHS against the quark
     mass, with one set of massless eigenpairs (lambda_i = eps_i + 4 m^2; Fig. 1
-    analogue)."""
+    analogue).
+    cheby: eigensolve time against the Chebyshev filter degree."""
     import numpy as np
     import torch
 
@@ -641,6 +642,27 @@ def run_sweep(a):
         plain = solve(H.hisq_default_solve_params(deflate=0, **base))
         print(json.dumps({"sweep": "delta_tr", "lattice": list(dims), "mass": m0, "n_ev": n_ev,
                           "plain_cg": plain, "rows": rows}), flush=True)
+    elif a.sweep == "cheby":
+        # eigensolve time against the Chebyshev filter degree (0 = no filter),
+        # and the deflated solve that the pairs give
+        rows = []
+        for deg in (0, 20, 40, 60, 100, 150):
+            ep = H.hisq_default_eig_params(n_ev=n_ev, n_kr=max(int(1.5 * n_ev), n_ev + 32), tol=a.eig_tol,
+                                           max_restarts=200 if deg == 0 else 100, cheby_degree=deg, a_min=a.amin)
+            torch.cuda.synchronize()
+            t0 = time.time()
+            try:
+                eps, nconv = H.hisq_eigensolve(ctx, ep)
+            except H.HisqError as e:
+                rows.append(dict(cheby_degree=deg, error=str(e)))
+                continue
+            torch.cuda.synchronize()
+            t_eig = time.time() - t0
+            r = solve(H.hisq_default_solve_params(deflate=1, **base))
+            rows.append(dict(cheby_degree=deg, eigensolve_seconds=round(t_eig, 2), converged=int(nconv),
+                             eps_min=float(eps[0]), eps_max=float(eps[-1]), deflated=r))
+        print(json.dumps({"sweep": "cheby", "lattice": list(dims), "mass": m0, "n_ev": n_ev, "rows": rows}),
+              flush=True)
     else:
         eigensolve(32)
         rows = []

@@ -32,7 +32,9 @@ def write_traffic(report: str, config: str, key: str, out: str, command: str) ->
     col = {n: hdr.index(n) for n in ("Kernel Name", "dram__bytes_read.sum", "dram__bytes_write.sum")}
     units = rows[1]
     scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
-    vh = I.volume(I.lattice_config(config)["dims"]) // 2
+    dims = I.lattice_config(config)["dims"]
+    dims_s = f"{dims[0]}^3x{dims[3]}"
+    vh = I.volume(dims) // 2
     per_site = {}
     for r in data:
         name = r[col["Kernel Name"]]
@@ -43,7 +45,7 @@ def write_traffic(report: str, config: str, key: str, out: str, command: str) ->
                 for m in ("dram__bytes_read.sum", "dram__bytes_write.sum"))
         per_site.setdefault(f"{kind}_{key}", []).append(b / vh)
     doc = {"what": f"DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per output site of the sloppy "
-                   f"Dslash kernels, from one ncu capture on the {config} lattice (Vh = {vh}); traffic scales with "
+                   f"Dslash kernels, from one ncu capture on the {dims_s} lattice (Vh = {vh}); traffic scales with "
                    f"the number of output sites, so the benchmark multiplies by its own Vh",
            "command": command, "kernel_source_hash": dslash_source_hash(),
            "dram_bytes_per_output_site": {k: round(sum(v) / len(v), 1) for k, v in per_site.items()}}
