@@ -124,6 +124,9 @@ typedef struct {
     double a_max;            /* > 0: given; <= 0: 1.1 x a power-iteration estimate  */
     int storage_precision;   /* eigenvector storage: 32, 16 or HISQ_PREC_BF16 (15)    */
     uint64_t seed;           /* start vector                                        */
+    int block_size;          /* 1: thick-restart Lanczos; b = 2..64: block thick-restart
+                                Lanczos with b vectors per step, the operator applied to
+                                the whole block at once (the paper's outlook, Section 4) */
 } hisq_eig_params;
 
 /* Fill the structs with the paper's defaults (Section 3: delta_rd = 0.1,

@@ -179,6 +179,7 @@ void hisq_default_eig_params(hisq_eig_params *p)
     p->a_max = 0;
     p->storage_precision = 32;
     p->seed = 1234;
+    p->block_size = 1;
 }
 
 hisq_status hisq_create(const int dims[4], int t_antiperiodic, int device, void *cuda_stream, hisq_ctx **out)

@@ -257,6 +257,9 @@ static hisq_status store_eigvecs(hisq_ctx *ctx, int n, const void *vf32, int pre
     return HISQ_OK;
 }
 
+hisq_status block_trlm(hisq_ctx *ctx, const hisq_eig_params *P, int b, int n_ev, int n_kr, int n_keep, int deg,
+                       double amin, double amax, void *B, int *conv_out);
+
 // ------------------------------------------------------------ TRLM
 static hisq_status trlm(hisq_ctx *ctx, const hisq_eig_params *P, int *n_conv, double *eps_out)
 {
@@ -278,7 +281,8 @@ static hisq_status trlm(hisq_ctx *ctx, const hisq_eig_params *P, int *n_conv, do
     const size_t Lf = size_t(6) * Vh;
     size_t chunk = (size_t(256) << 20) / (sizeof(float) * size_t(nrot));
     chunk = std::max<size_t>(128, std::min(Lf, chunk) / 128 * 128);
-    char *B = (char *)dev_alloc(ctx, sf * (n_kr + 1));
+    const int bs = P->block_size > 1 ? P->block_size : 1;
+    char *B = (char *)dev_alloc(ctx, sf * (n_kr + bs));
     char *R = (char *)dev_alloc(ctx, sizeof(float) * chunk * nrot);
     char *wk = (char *)dev_alloc(ctx, sf * 4);
     double *coef = (double *)dev_alloc(ctx, sizeof(double) * 2 * (n_kr + 1));
@@ -292,7 +296,7 @@ static hisq_status trlm(hisq_ctx *ctx, const hisq_eig_params *P, int *n_conv, do
             cudaStreamSynchronize(c->stream);
             for (int i = 0; i < 5; i++) dev_free(c, p[i], s[i]);
         }
-    } guard{ctx, {B, R, wk, coef, Yd}, {sf * (n_kr + 1), sizeof(float) * chunk * nrot, sf * 4, sizeof(double) * 2 * (n_kr + 1), sizeof(double) * size_t(n_kr) * nrot}};
+    } guard{ctx, {B, R, wk, coef, Yd}, {sf * (n_kr + bs), sizeof(float) * chunk * nrot, sf * 4, sizeof(double) * 2 * (n_kr + 1), sizeof(double) * size_t(n_kr) * nrot}};
     if (!B || !R || !wk || !coef || !Yd) return HISQ_ERR_OOM;
     void *tmp_odd = get_buf(ctx, BUF_TMP, spinor_bytes(32, Vh));
     if (!tmp_odd) return HISQ_ERR_OOM;
@@ -384,6 +388,17 @@ static hisq_status trlm(hisq_ctx *ctx, const hisq_eig_params *P, int *n_conv, do
     ctx->last_window[0] = amin;
     ctx->last_window[1] = amax;
     const bool want_largest = deg > 0;
+
+    if (bs > 1) {
+        // block thick-restart Lanczos (block_eig.cu); Ritz vectors end in B[0 .. n_ev)
+        int conv = 0;
+        TRY(block_trlm(ctx, P, bs, n_ev, n_kr, n_keep, deg, amin, amax, B, &conv));
+        TRY(store_eigvecs(ctx, n_ev, B, P->storage_precision, nullptr, nullptr));
+        if (n_conv) *n_conv = conv;
+        if (eps_out)
+            for (int i = 0; i < n_ev; i++) eps_out[i] = ctx->eig.eps[i];
+        return HISQ_OK;
+    }
 
     // start vector
     TRY(start(P->seed));

@@ -921,6 +921,11 @@ hisq_status launch_mrhs_dslash_tt(hisq_ctx *ctx, int prec, int link_prec, void *
 hisq_status launch_mrhs_dslash_update(hisq_ctx *ctx, int prec, int link_prec, void *tmp, void *p, void *x, void *r,
                                       int kact);
 hisq_status launch_mrhs_p_update(hisq_ctx *ctx, int prec, void *r, void *p, int kact);
+// blocks of k ordinary FP32 fields (eigensolver): slots 0..k-1 active, and
+// out_j = a x_j + b y_j + c D(in_j) on output parity par (x, y nullable)
+hisq_status mrhs_set_identity(hisq_ctx *ctx, int k);
+hisq_status launch_mrhs_dslash_lin(hisq_ctx *ctx, int par, const void *in, void *out, double a, const void *x,
+                                   double b, const void *y, double c, int k);
 
 // link ingest (ingest.cu)
 hisq_status ingest_links(hisq_ctx *ctx, const double *fat_dev, const double *lng_dev, int recon,

@@ -9,6 +9,7 @@
 // Per-RHS reductions are deterministic: lanes by a fixed shuffle tree, warps in
 // a fixed order, blocks by the last block in block order.
 #include <algorithm>
+#include <cstddef>
 #include <functional>
 
 #include "internal.cuh"
@@ -162,6 +163,40 @@ struct BEpiCG {
         xj.store(cb, xv);
         rj.store(cb, rv);
         red += double(rv.norm2());
+    }
+};
+
+// out_j = a x_j + b y_j + c acc (x, y nullable), FP32 fields; no reduction
+struct BEpiLin {
+    BatchF<SpinorF> out, x, y;
+    float a, b, c;
+    bool hx, hy;
+    template <typename R>
+    __device__ __forceinline__ void operator()(int cb, int j, const CVec<R> &acc, double &) const
+    {
+        CVec<float> o;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            o.re[i] = c * float(acc.re[i]);
+            o.im[i] = c * float(acc.im[i]);
+        }
+        if (hx) {
+            const CVec<float> v = x.at(j).load(cb);
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                o.re[i] = fmaf(a, v.re[i], o.re[i]);
+                o.im[i] = fmaf(a, v.im[i], o.im[i]);
+            }
+        }
+        if (hy) {
+            const CVec<float> v = y.at(j).load(cb);
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                o.re[i] = fmaf(b, v.re[i], o.re[i]);
+                o.im[i] = fmaf(b, v.im[i], o.im[i]);
+            }
+        }
+        out.at(j).store(cb, o);
     }
 };
 
@@ -459,6 +494,31 @@ hisq_status launch_mrhs_dslash_update(hisq_ctx *ctx, int prec, int link_prec, vo
     }
     }
     return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched sloppy precision must be 32 or 16");
+}
+
+// active slots 0..k-1 = right-hand sides 0..k-1 (a block of ordinary fields)
+hisq_status mrhs_set_identity(hisq_ctx *ctx, int k)
+{
+    if (k < 1 || k > kMaxBatch) return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched operator: 1..64 fields");
+    int buf[kMaxBatch + 1];
+    buf[0] = k;
+    for (int q = 0; q < k; q++) buf[1 + q] = q;
+    static_assert(offsetof(BatchScalars, idx) == offsetof(BatchScalars, kact) + sizeof(int), "kact, idx adjacent");
+    HISQ_CUDA(cudaMemcpyAsync(&ctx->bscal->kact, buf, sizeof(int) * (1 + k), cudaMemcpyHostToDevice, ctx->stream));
+    return HISQ_OK;
+}
+
+// out_j = a x_j + b y_j + c D(in_j) on output parity par for the k FP32 fields
+// of a block (slots 0..k-1 active, mrhs_set_identity); x, y nullable
+hisq_status launch_mrhs_dslash_lin(hisq_ctx *ctx, int par, const void *in, void *out, double a, const void *x,
+                                   double b, const void *y, double c, int k)
+{
+    const int Vh = ctx->g.Vh;
+    BEpiLin epi{batchf<SpinorF>(out, Vh, 32), batchf<SpinorF>(const_cast<void *>(x), Vh, 32),
+                batchf<SpinorF>(const_cast<void *>(y), Vh, 32), float(a), float(b), float(c), x != nullptr,
+                y != nullptr};
+    return run_mrhs(ctx, par, 32, 32, batchf<SpinorF>(const_cast<void *>(in), Vh, 32), k, epi,
+                    batch_red(ctx, BFIN_STORE), false);
 }
 
 // (3) p_j = r_j + beta_j p_j, pp_j (the shape of the batch's Dslash)

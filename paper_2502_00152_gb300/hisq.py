@@ -63,7 +63,8 @@ class hisq_solve_stats(ctypes.Structure):
 class hisq_eig_params(ctypes.Structure):
     _fields_ = [("n_ev", ctypes.c_int), ("n_kr", ctypes.c_int), ("n_keep", ctypes.c_int), ("tol", ctypes.c_double),
                 ("max_restarts", ctypes.c_int), ("cheby_degree", ctypes.c_int), ("a_min", ctypes.c_double),
-                ("a_max", ctypes.c_double), ("storage_precision", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("a_max", ctypes.c_double), ("storage_precision", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("block_size", ctypes.c_int)]
 
 
 _lib = None

@@ -48,6 +48,33 @@ def test_trlm_eigenvalues_match_dense(lat, cheby):
         assert np.all(project_parity(dims, v, 1) == 0)
 
 
+@pytest.mark.parametrize("block,cheby", [(4, 0), (8, 12), (16, 12)])
+def test_block_trlm_eigenvalues_match_dense(lat, block, cheby):
+    """Block thick-restart Lanczos (the operator applied to `block` fields at a
+    time with the batched Dslash): same eigenpairs as dense diagonalisation."""
+    dims, m, ctx, o, w, vecs = lat
+    n_ev = 16
+    prm = H.hisq_default_eig_params(n_ev=n_ev, n_kr=64, tol=1e-6, max_restarts=300, cheby_degree=cheby,
+                                    a_min=float(w[30]) if cheby else 0.0, a_max=0.0, seed=11, block_size=block)
+    eps, nconv = H.hisq_eigensolve(ctx, prm)
+    assert nconv == n_ev
+    ok = _clusters_ok(w, n_ev)
+    assert np.max(np.abs(eps[ok] - w[ok]) / w[ok]) <= 1e-8
+    for i in range(n_ev):
+        v = H.hisq_get_eigvec(ctx, i)
+        th, res = o.rayleigh(0.0, v)
+        assert abs(th - eps[i]) <= 1e-8 * eps[i]
+        assert res <= 1e-4 * w[-1]
+        assert np.all(project_parity(dims, v, 1) == 0)
+
+
+def test_block_trlm_rejects_small_basis(lat):
+    dims, m, ctx, o, w, vecs = lat
+    prm = H.hisq_default_eig_params(n_ev=8, n_kr=14, block_size=8)
+    with pytest.raises(H.HisqError):
+        H.hisq_eigensolve(ctx, prm)
+
+
 def test_mass_shift_of_stored_eigenvalues(lat):
     """lambda_i = eps_i + 4 m^2 (Eq. 3): deflating with the stored pairs equals
     the oracle's deflation with the dense eigenvectors of A_ee(m)."""
