@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--cheby", type=int, default=60)
     ap.add_argument("--amin", type=float, default=-2.0)
     ap.add_argument("--eig-tol", type=float, default=1e-6)
+    ap.add_argument("--eig-block", type=int, default=1, help="eigensolver block size (1: thick-restart Lanczos)")
     ap.add_argument("--eig-prec", type=int, default=None,
                     help="eigenvector storage: 32 (FP32), 16 (FP16 + per-site scale), 15 (BF16); "
                          "default 32, BF16 for the batched 32^3x64 workload")
@@ -216,12 +217,14 @@ def run_ours(a):
     eig = {}
     if n_ev > 0:
         ep = H.hisq_default_eig_params(n_ev=n_ev, n_kr=n_kr, tol=a.eig_tol, max_restarts=100, cheby_degree=a.cheby,
-                                       a_min=a.amin, a_max=0.0, storage_precision=a.eig_prec, seed=1000 + rank)
+                                       a_min=a.amin, a_max=0.0, storage_precision=a.eig_prec, seed=1000 + rank,
+                                       block_size=a.eig_block)
         torch.cuda.synchronize()
         t0 = time.time()
         eps, nconv = H.hisq_eigensolve(ctx, ep)
         torch.cuda.synchronize()
-        eig = dict(seconds=time.time() - t0, n_ev=n_ev, n_kr=n_kr, converged=nconv, cheby_degree=a.cheby,
+        eig = dict(seconds=time.time() - t0, n_ev=n_ev, n_kr=n_kr, block_size=a.eig_block, converged=nconv,
+                   cheby_degree=a.cheby,
                    eps_min=float(eps[0]), eps_max=float(eps[-1]), storage=a.eig_prec)
 
     # sources: resident in HBM before the timed region (FP64 full-lattice fields)
