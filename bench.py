@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--cheby", type=int, default=60)
     ap.add_argument("--amin", type=float, default=-2.0)
     ap.add_argument("--eig-tol", type=float, default=1e-6)
-    ap.add_argument("--eig-block", type=int, default=1, help="eigensolver block size (1: thick-restart Lanczos)")
+    ap.add_argument("--eig-block", type=int, default=64,
+                    help="eigensolver block size (1: thick-restart Lanczos; b: block thick-restart Lanczos)")
     ap.add_argument("--eig-prec", type=int, default=None,
                     help="eigenvector storage: 32 (FP32), 16 (FP16 + per-site scale), 15 (BF16); "
                          "default 32, BF16 for the batched 32^3x64 workload")

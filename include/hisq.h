@@ -126,7 +126,9 @@ typedef struct {
     uint64_t seed;           /* start vector                                        */
     int block_size;          /* 1: thick-restart Lanczos; b = 2..64: block thick-restart
                                 Lanczos with b vectors per step, the operator applied to
-                                the whole block at once (the paper's outlook, Section 4) */
+                                the whole block at once (the paper's outlook, Section 4);
+                                reduced to (n_kr - n_ev) / 2 when larger, and n_kr,
+                                n_keep rounded to the block grid                      */
 } hisq_eig_params;
 
 /* Fill the structs with the paper's defaults (Section 3: delta_rd = 0.1,
