@@ -266,6 +266,14 @@ hisq_status hisq_set_profiling(hisq_ctx *ctx, int on);
  * injection off; the context stays usable.  Nothing is done on the device. */
 hisq_status hisq_inject_alloc_failure(hisq_ctx *ctx, int after);
 
+/* Bounds checking (a stand-in for a memory checker): in a library built with
+ * -DHISQ_BOUNDS_CHECK every neighbour and site index is range-checked in the
+ * kernels; an index out of range sets a flag and is replaced by 0 (the access
+ * stays inside the array).  *flag = 1 if any index was out of range since the
+ * last call (the flag is then cleared).  A normal build returns
+ * HISQ_ERR_STATE (its indices are not checked); *flag is still written. */
+hisq_status hisq_bounds_violations(hisq_ctx *ctx, int *flag);
+
 /* ---- learned initial guess: gauge-covariant parallel-transport layers.
  * The paper has no learned part; these entry points serve a small network that
  * predicts the CG starting vector (CG still runs to the same true residual).

@@ -225,6 +225,8 @@ hisq_status hisq_create(const int dims[4], int t_antiperiodic, int device, void 
         if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(HISQ_ERR_CUDA);
         ctx->own_stream = true;
     }
+    ctx->g.oob = (int *)dev_alloc(ctx, sizeof(int));
+    if (!ctx->g.oob || cudaMemset(ctx->g.oob, 0, sizeof(int)) != cudaSuccess) return fail(HISQ_ERR_OOM);
     ctx->max_red_blocks = ctx->num_sms * 16;
     ctx->partials = (double *)dev_alloc(ctx, sizeof(double) * ctx->max_red_blocks * kMaxRedVals);
     ctx->ticket = (unsigned int *)dev_alloc(ctx, 256);
@@ -263,6 +265,7 @@ void hisq_destroy(hisq_ctx *ctx)
     for (int i = 0; i < BUF_COUNT; i++) cudaFree(ctx->bufs[i]);
     cudaFree(ctx->eig.vecs);
     cudaFree(ctx->partials);
+    cudaFree(ctx->g.oob);
     cudaFree(ctx->ticket);
     cudaFree(ctx->scal);
     if (ctx->monitor_h) cudaFreeHost(ctx->monitor_h);
@@ -382,6 +385,20 @@ hisq_status hisq_apply_dslash(hisq_ctx *ctx, int out_parity, int precision, int 
     HISQ_CUDA(cudaMemsetAsync(full, 0, size_t(ctx->g.V) * 48, ctx->stream));
     TRY(launch_scatter_parity(ctx, b, precision, out_parity, full));
     return download_full(ctx, full, out);
+}
+
+hisq_status hisq_bounds_violations(hisq_ctx *ctx, int *flag)
+{
+    if (!ctx || !flag) return HISQ_ERR_INVALID_ARG;
+    HISQ_CUDA(cudaSetDevice(ctx->device));
+    HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    HISQ_CUDA(cudaMemcpy(flag, ctx->g.oob, sizeof(int), cudaMemcpyDeviceToHost));
+    HISQ_CUDA(cudaMemset(ctx->g.oob, 0, sizeof(int)));
+#ifdef HISQ_BOUNDS_CHECK
+    return HISQ_OK;
+#else
+    return set_err(ctx, HISQ_ERR_STATE, "library built without HISQ_BOUNDS_CHECK: indices are not checked");
+#endif
 }
 
 hisq_status hisq_inject_alloc_failure(hisq_ctx *ctx, int after)

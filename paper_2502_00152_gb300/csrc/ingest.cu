@@ -91,7 +91,7 @@ __global__ void k_ingest(Geom g, int par, const double2 *__restrict__ fat, const
             // backward source site x - n mu
             int cb_[4] = {c[0], c[1], c[2], c[3]};
             cb_[mu] = (c[mu] - n + L) % L;
-            const int sb = full_site(g, cb_);
+            const int sb = checked_index(g, full_site(g, cb_), g.V);
             double sf = eta, sbk = -eta;
             if (mu == 3 && g.t_antiperiodic) {
                 if (c[3] + n >= g.T) sf = -sf;

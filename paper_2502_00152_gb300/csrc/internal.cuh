@@ -110,7 +110,24 @@ struct Geom {
     int V;
     int t_antiperiodic;
     int stride[4];   // 1, X, XY, XYZ (full-lattice site index)
+    int *oob;        // device flag set by out-of-range indices (HISQ_BOUNDS_CHECK builds)
 };
+
+// Index check of the bounds-checking build (-DHISQ_BOUNDS_CHECK): an index
+// outside [0, n) sets the context's flag and is replaced by 0, so the access
+// stays inside the array; the normal build compiles to the index itself.
+#ifdef HISQ_BOUNDS_CHECK
+__device__ __forceinline__ int checked_index(const Geom &g, int i, int n)
+{
+    if (i < 0 || i >= n) {
+        if (g.oob) atomicOr(g.oob, 1);
+        return 0;
+    }
+    return i;
+}
+#else
+__device__ __forceinline__ int checked_index(const Geom &, int i, int) { return i; }
+#endif
 
 // coordinates of checkerboard site cb of parity `par` (cb = s >> 1)
 __device__ __forceinline__ void cb_coords(const Geom &g, int par, int cb, int c[4])
@@ -148,7 +165,7 @@ __device__ __forceinline__ int nb_cb(const Geom &g, const int c[4], int s, int m
     int cn = cm + d;
     cn += (cn < 0) ? L : 0;
     cn -= (cn >= L) ? L : 0;
-    return (s + (cn - cm) * stride_of(g, mu)) >> 1;
+    return checked_index(g, (s + (cn - cm) * stride_of(g, mu)) >> 1, g.Vh);
 }
 
 __device__ __forceinline__ int full_site(const Geom &g, const int c[4])

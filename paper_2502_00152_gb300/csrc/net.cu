@@ -41,7 +41,7 @@ __device__ __forceinline__ void net_transport(const Geom &g, const float4 *links
     int cn[4] = {c[0], c[1], c[2], c[3]};
     const int L = dim_of(g, mu);
     cn[mu] = d == 0 ? (c[mu] + 1 == L ? 0 : c[mu] + 1) : (c[mu] == 0 ? L - 1 : c[mu] - 1);
-    const int sn = full_site(g, cn);
+    const int sn = checked_index(g, full_site(g, cn), g.V);
     float2 v[3];
 #pragma unroll
     for (int i = 0; i < 3; i++) v[i] = ch[size_t(sn) * 3 + i];

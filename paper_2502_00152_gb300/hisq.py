@@ -18,7 +18,8 @@ from typing import Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libhisq.so")
+# HISQ_LIBRARY selects another build of the library (e.g. the bounds-checking one)
+LIB_PATH = os.environ.get("HISQ_LIBRARY") or os.path.join(_HERE, "libhisq.so")
 
 HISQ_OK = 0
 HISQ_ERR_INVALID_ARG = 1
@@ -98,6 +99,7 @@ _PROTOS = [
     ("hisq_load_eigvecs", ctypes.c_int, [_CTX, ctypes.c_char_p]),
     ("hisq_set_profiling", ctypes.c_int, [_CTX, ctypes.c_int]),
     ("hisq_inject_alloc_failure", ctypes.c_int, [_CTX, ctypes.c_int]),
+    ("hisq_bounds_violations", ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int)]),
     ("hisq_device_bytes", ctypes.c_size_t, [_CTX]),
     ("hisq_kernel_launches", ctypes.c_ulonglong, [_CTX]),
 ]
@@ -323,6 +325,14 @@ def hisq_save_eigvecs(ctx: Context, path: str) -> None:
 
 def hisq_load_eigvecs(ctx: Context, path: str) -> None:
     _check(ctx.handle, load_library().hisq_load_eigvecs(ctx.handle, path.encode()))
+
+
+def hisq_bounds_violations(ctx: Context) -> int:
+    """1 if a kernel of the bounds-checking build met an out-of-range index since
+    the last call (raises HisqError with HISQ_ERR_STATE on a normal build)."""
+    f = ctypes.c_int(0)
+    _check(ctx.handle, load_library().hisq_bounds_violations(ctx.handle, ctypes.byref(f)))
+    return f.value
 
 
 def hisq_inject_alloc_failure(ctx: Context, after: int) -> None:
