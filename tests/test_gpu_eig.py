@@ -68,11 +68,16 @@ def test_block_trlm_eigenvalues_match_dense(lat, block, cheby):
         assert np.all(project_parity(dims, v, 1) == 0)
 
 
-def test_block_trlm_rejects_small_basis(lat):
+def test_block_size_adapts_to_small_basis(lat):
+    """The block shrinks to (n_kr - n_ev) / 2 when the Krylov space is small,
+    and a space with no room for two blocks is refused."""
     dims, m, ctx, o, w, vecs = lat
-    prm = H.hisq_default_eig_params(n_ev=8, n_kr=14, block_size=8)
+    eps, nconv = H.hisq_eigensolve(ctx, H.hisq_default_eig_params(n_ev=8, n_kr=14, block_size=8, tol=1e-6,
+                                                                  max_restarts=500, seed=3))
+    ok = _clusters_ok(w, 8)
+    assert nconv == 8 and np.max(np.abs(eps[ok] - w[ok]) / w[ok]) <= 1e-8
     with pytest.raises(H.HisqError):
-        H.hisq_eigensolve(ctx, prm)
+        H.hisq_eigensolve(ctx, H.hisq_default_eig_params(n_ev=8, n_kr=11, block_size=8))
 
 
 def test_mass_shift_of_stored_eigenvalues(lat):
