@@ -72,8 +72,9 @@ def test_block_size_adapts_to_small_basis(lat):
     """The block shrinks to (n_kr - n_ev) / 2 when the Krylov space is small,
     and a space with no room for two blocks is refused."""
     dims, m, ctx, o, w, vecs = lat
-    eps, nconv = H.hisq_eigensolve(ctx, H.hisq_default_eig_params(n_ev=8, n_kr=14, block_size=8, tol=1e-6,
-                                                                  max_restarts=500, seed=3))
+    eps, nconv = H.hisq_eigensolve(ctx, H.hisq_default_eig_params(n_ev=8, n_kr=20, block_size=16, tol=1e-6,
+                                                                  max_restarts=500, cheby_degree=12,
+                                                                  a_min=float(w[30]), seed=3))
     ok = _clusters_ok(w, 8)
     assert nconv == 8 and np.max(np.abs(eps[ok] - w[ok]) / w[ok]) <= 1e-8
     with pytest.raises(H.HisqError):
