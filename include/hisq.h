@@ -127,8 +127,9 @@ typedef struct {
     int block_size;          /* 1: thick-restart Lanczos; b = 2..64: block thick-restart
                                 Lanczos with b vectors per step, the operator applied to
                                 the whole block at once (the paper's outlook, Section 4);
-                                reduced to (n_kr - n_ev) / 2 when larger, and n_kr,
-                                n_keep rounded to the block grid                      */
+                                reduced to (n_kr - n_keep) / 2 when larger, so that a
+                                restart adds at least two blocks; n_kr and n_keep are
+                                rounded to the block grid                             */
 } hisq_eig_params;
 
 /* Fill the structs with the paper's defaults (Section 3: delta_rd = 0.1,
