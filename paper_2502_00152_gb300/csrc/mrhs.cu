@@ -201,6 +201,25 @@ struct BEpiLin {
 };
 
 // ------------------------------------------------------------- the kernel
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+__device__ __forceinline__ void prefetch_long(const LinksF12 &L, int mu, int i)
+{
+    if (!L.base) return;
+    const float4 *q = L.base + size_t(mu * 6) * L.Vh + i;
+#pragma unroll
+    for (int k = 0; k < 6; k++) prefetch_l2(q + size_t(k) * L.Vh);
+}
+__device__ __forceinline__ void prefetch_long(const LinksF8 &L, int mu, int i)
+{
+    const float4 *q = L.base + size_t(mu * 4) * L.Vh + i;
+#pragma unroll
+    for (int k = 0; k < 4; k++) prefetch_l2(q + size_t(k) * L.Vh);
+}
+
 template <int R, class S, class Lk, class L12T, bool R12, class Epi>
 __global__ void __launch_bounds__(512, 1)
     k_dslash_mrhs(Geom g, int par, Lk L, L12T L12, float c3, BatchF<S> in, const BatchScalars *scal, MrhsTile tl,
@@ -234,6 +253,12 @@ __global__ void __launch_bounds__(512, 1)
         for (int mu = 0; mu < 4; mu++) {
             const int f1 = nb_cb(g, c, s, mu, +1), b1 = nb_cb(g, c, s, mu, -1);
             const int f3 = nb_cb(g, c, s, mu, +3), b3 = nb_cb(g, c, s, mu, -3);
+            // the next direction's links (read from DRAM once per launch) are
+            // requested into L2 while this direction is computed
+            if (mu < 3) {
+                L.prefetch(mu + 1, cb);
+                prefetch_long(L12, mu + 1, cb);
+            }
             CMat<Rl> f, b;
             L.load(mu, 0, cb, f, b);
 #pragma unroll
@@ -369,6 +394,12 @@ struct LinksFvB {
     int Vh;
     int nk;
     typedef float real;
+    __device__ __forceinline__ void prefetch(int mu, int i) const
+    {
+        const float4 *q = base + size_t((mu * nk) * 9) * Vh + i;
+#pragma unroll
+        for (int k = 0; k < 9; k++) prefetch_l2(q + size_t(k) * Vh);
+    }
     __device__ __forceinline__ void load(int mu, int kind, int i, CMat<float> &f, CMat<float> &b) const
     {
         const float4 *q = base + size_t((mu * nk + kind) * 9) * Vh + i;
