@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--sloppy", type=int, default=16, help="sloppy colour-vector storage: 32 or 16")
     ap.add_argument("--recon", type=int, default=12, help="long links: 18 reals, 12 (two rows + SU(3) row) or 8 (a2, a3, b1 and two phases)")
     ap.add_argument("--links", type=int, default=32, help="sloppy link storage: 32 or 16")
+    ap.add_argument("--reliable", type=int, choices=[64, 48], default=None,
+                    help="reliable-update residual arithmetic: 64 (FP64) or 48 (double-float on the FP32 units, "
+                         "certified in FP64); default 48, and 64 for c5 (no room for the double-float links)")
     ap.add_argument("--n-ev", type=int, default=None)
     ap.add_argument("--n-kr", type=int, default=None)
     ap.add_argument("--cheby", type=int, default=60)
@@ -245,10 +248,12 @@ def run_ours(a):
     if keep_links[0] is None:
         del fat, lng
     psi_dev = torch.zeros_like(eta_dev[0])
+    rel_prec = a.reliable if a.reliable is not None else (64 if a.config == "c5" else H.HISQ_PREC_DF64)
     prm_defl = H.hisq_default_solve_params(tol=tol, precision_sloppy=a.sloppy, link_precision_sloppy=a.links,
-                                           deflate=1 if n_ev > 0 else 0, compute_full_residual=1)
+                                           deflate=1 if n_ev > 0 else 0, compute_full_residual=1,
+                                           precision_reliable=rel_prec)
     prm_plain = H.hisq_default_solve_params(tol=tol, precision_sloppy=a.sloppy, link_precision_sloppy=a.links,
-                                            deflate=0, compute_full_residual=1)
+                                            deflate=0, compute_full_residual=1, precision_reliable=rel_prec)
 
     def solve(k, prm):
         st, status = H.hisq_solve_device(ctx, eta_dev[k], psi_dev, kps, prm)
@@ -307,6 +312,21 @@ def run_ours(a):
         e2e_ms.append((time.perf_counter() - t0) * 1e3 / kps)
         if status != H.HISQ_OK:
             raise RuntimeError("host-API solve did not converge")
+
+    # the same solves with the paper's FP64 reliable updates (comparison)
+    fp64_rel = None
+    if rel_prec != 64:
+        prm64 = H.hisq_default_solve_params(tol=tol, precision_sloppy=a.sloppy, link_precision_sloppy=a.links,
+                                            deflate=1 if n_ev > 0 else 0, compute_full_residual=1,
+                                            precision_reliable=64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s64 = solve(a.warmup, prm64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64_rel = {"ms_per_rhs": round(e0.elapsed_time(e1) / kps, 3), "iterations": s64["iterations"],
+                    "reliable_updates": s64["reliable_updates"], "true_residual_max": s64["full_residual"]}
 
     # Dslash roofline from the event-timed kernels of the timed solves
     it = sum(s["profiled_iterations"] for s in stats)
@@ -374,8 +394,9 @@ def run_ours(a):
         "data": "synthetic",
         "config": {
             "workload": f"HISQ {dims[0]}^3x{dims[3]}, m={m}, {n_ev} eigenpairs ({eig_name}), deflated "
-                        f"mixed-precision CG (FP{a.sloppy} vectors, FP{a.links} links recon {a.recon}, FP64 "
-                        f"reliable updates), "
+                        f"mixed-precision CG (FP{a.sloppy} vectors, FP{a.links} links recon {a.recon}, "
+                        + ("FP64 reliable updates" if rel_prec == 64 else
+                           "double-float reliable updates, final residual confirmed in FP64") + "), "
                         + ("1 Gaussian RHS per step" if kps == 1 else
                            (f"{kps} RHS per step ({kps // 3} Gaussian sources x 3 colours), batched"
                             if a.config == "c5" else f"{kps} Z2 wall RHS per step, batched"))
@@ -391,6 +412,8 @@ def run_ours(a):
         "gpu_launches": int(launches),
         "clocks": clk,
         "plain_cg_ms_per_rhs": round(plain_ms, 3),
+        "reliable_updates_arithmetic": "fp64" if rel_prec == 64 else "double-float (FP32 hi+lo), FP64-confirmed",
+        "fp64_reliable_updates": fp64_rel,
         "iterations_deflated": [s["iterations"] for s in stats],
         "iterations_plain": [s["iterations"] for s in plain],
         "reliable_updates": [s["reliable_updates"] for s in stats],

@@ -61,12 +61,17 @@ typedef enum {
     HISQ_ERR_STATE = 7          /* call order violated (e.g. solve before links)   */
 } hisq_status;
 
-/* Storage precisions.  Arithmetic is FP64 for HISQ_PREC_DOUBLE and FP32 otherwise. */
+/* Storage precisions.  Arithmetic is FP64 for HISQ_PREC_DOUBLE, double-float for
+ * HISQ_PREC_DF64 and FP32 otherwise. */
 typedef enum {
     HISQ_PREC_DOUBLE = 64,
     HISQ_PREC_SINGLE = 32,
     HISQ_PREC_HALF = 16, /* FP16 values with one FP32 scale per site (colour vectors) */
-    HISQ_PREC_BF16 = 15  /* BF16 values, 12 B per site; eigenvector storage only     */
+    HISQ_PREC_BF16 = 15, /* BF16 values, 12 B per site; eigenvector storage only     */
+    HISQ_PREC_DF64 = 48  /* double-float: each real the sum hi + lo of two FP32
+                            numbers (about 48 significant bits), FP32 arithmetic
+                            with exact products and error-carrying sums; the
+                            reliable-update residual and the test operators only */
 } hisq_precision;
 
 /* Parameters of a propagator solve (Sections 2 and 3). */
@@ -91,6 +96,14 @@ typedef struct {
     int guess;               /* 1: psi holds an initial guess on entry (its even
                                 sites); the solve starts from it, deflating its
                                 residual when deflation is on                      */
+    int precision_reliable;  /* arithmetic of the reliable-update residual
+                                b - A x: 64 (FP64, Section 3) or HISQ_PREC_DF64
+                                (double-float on the FP32 units; a residual that
+                                meets the tolerance is recomputed in FP64 before
+                                convergence is reported, and the rest of that
+                                right-hand side's solve uses FP64 if it is not
+                                confirmed).  The double-float links take as much
+                                device memory as the FP64 copy (2304 B per site). */
 } hisq_solve_params;
 
 /* Per right-hand-side results of a solve. */
@@ -168,13 +181,15 @@ hisq_status hisq_set_mass(hisq_ctx *ctx, double m);
 /* out_parity sites of `out` = D applied to the opposite-parity sites of `in`
  * (host full-lattice fields); the other parity of `out` is set to zero.
  * precision: colour-vector storage (64, 32, 16); link_precision: link storage
- * (64 with precision 64; 32 or 16 otherwise; arithmetic FP32).
- * Test and diagnostic entry point. */
+ * (64 with precision 64; 32 or 16 otherwise; arithmetic FP32).  Precision and
+ * link precision HISQ_PREC_DF64 apply the double-float operator of the
+ * reliable updates to the FP64 input.  Test and diagnostic entry point. */
 hisq_status hisq_apply_dslash(hisq_ctx *ctx, int out_parity, int precision, int link_precision,
                               const double *in, double *out);
 
 /* Even sites of `out` = (M^dag M)_ee applied to the even sites of `in`
- * (= 4m^2 in_e - D_eo D_oe in_e); odd sites of `out` are zero. */
+ * (= 4m^2 in_e - D_eo D_oe in_e); odd sites of `out` are zero.  Precisions as
+ * for hisq_apply_dslash. */
 hisq_status hisq_apply_normal_op(hisq_ctx *ctx, int precision, int link_precision, const double *in,
                                  double *out);
 

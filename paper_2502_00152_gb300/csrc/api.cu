@@ -164,6 +164,7 @@ void hisq_default_solve_params(hisq_solve_params *p)
     p->compute_full_residual = 1;
     p->batch = 1;
     p->guess = 0;
+    p->precision_reliable = 64;
 }
 
 void hisq_default_eig_params(hisq_eig_params *p)
@@ -261,6 +262,7 @@ void hisq_destroy(hisq_ctx *ctx)
         cudaFree(ctx->links_f12[p]);
         cudaFree(ctx->links_h[p]);
         cudaFree(ctx->links_h12[p]);
+        cudaFree(ctx->links_df[p]);
     }
     for (int i = 0; i < BUF_COUNT; i++) cudaFree(ctx->bufs[i]);
     cudaFree(ctx->eig.vecs);
@@ -299,6 +301,8 @@ hisq_status hisq_load_links(hisq_ctx *ctx, const double *fat, const double *lng,
         ctx->links_h[p] = nullptr;
         dev_free(ctx, ctx->links_h12[p], size_t(Vh) * 4 * 6 * 8);
         ctx->links_h12[p] = nullptr;
+        dev_free(ctx, ctx->links_df[p], size_t(Vh) * 16 * 9 * 16);
+        ctx->links_df[p] = nullptr;
     }
     ctx->links_loaded = false;
     for (int p = 0; p < 2; p++) {
@@ -360,6 +364,7 @@ static hisq_status download_full(hisq_ctx *ctx, const double *dev, double *host)
 
 static bool bad_precisions(int prec, int link_prec)
 {
+    if (prec == HISQ_PREC_DF64 || link_prec == HISQ_PREC_DF64) return prec != link_prec;
     if (prec != 64 && prec != 32 && prec != 16) return true;
     if (link_prec != 64 && link_prec != 32 && link_prec != 16) return true;
     return (prec == 64) != (link_prec == 64);
@@ -371,7 +376,7 @@ hisq_status hisq_apply_dslash(hisq_ctx *ctx, int out_parity, int precision, int 
     if (!ctx) return HISQ_ERR_INVALID_ARG;
     if (!in || !out || (out_parity != 0 && out_parity != 1)) return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad argument");
     if (bad_precisions(precision, link_precision))
-        return set_err(ctx, HISQ_ERR_INVALID_ARG, "precisions must be 64/64 or 32|16 with 32|16 links");
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "precisions must be 64/64, 48/48 or 32|16 with 32|16 links");
     if (!ctx->links_loaded) return set_err(ctx, HISQ_ERR_STATE, "links not loaded");
     HISQ_CUDA(cudaSetDevice(ctx->device));
     const int Vh = ctx->g.Vh;
@@ -380,6 +385,16 @@ hisq_status hisq_apply_dslash(hisq_ctx *ctx, int out_parity, int precision, int 
     void *a = get_buf(ctx, BUF_TEST_B, spinor_bytes(precision, Vh));
     void *b = get_buf(ctx, BUF_TEST_C, spinor_bytes(precision, Vh));
     if (!a || !b) return HISQ_ERR_OOM;
+    if (precision == HISQ_PREC_DF64) {
+        void *d = get_buf(ctx, BUF_DF_X, spinor_bytes(HISQ_PREC_DF64, Vh));
+        if (!d) return HISQ_ERR_OOM;
+        TRY(launch_gather_parity(ctx, full, 1 - out_parity, 64, a));
+        TRY(launch_to_df64(ctx, (const double *)a, d));
+        TRY(launch_dslash_df_xpay(ctx, out_parity, d, (double *)b, 0, nullptr, 0, nullptr, 1.0, -1));
+        HISQ_CUDA(cudaMemsetAsync(full, 0, size_t(ctx->g.V) * 48, ctx->stream));
+        TRY(launch_scatter_parity(ctx, b, 64, out_parity, full));
+        return download_full(ctx, full, out);
+    }
     TRY(launch_gather_parity(ctx, full, 1 - out_parity, precision, a));
     TRY(launch_dslash(ctx, out_parity, precision, link_precision, a, b, 0, nullptr, 0, nullptr, 1.0, -1));
     HISQ_CUDA(cudaMemsetAsync(full, 0, size_t(ctx->g.V) * 48, ctx->stream));
@@ -413,7 +428,7 @@ hisq_status hisq_apply_normal_op(hisq_ctx *ctx, int precision, int link_precisio
     if (!ctx) return HISQ_ERR_INVALID_ARG;
     if (!in || !out) return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad argument");
     if (bad_precisions(precision, link_precision))
-        return set_err(ctx, HISQ_ERR_INVALID_ARG, "precisions must be 64/64 or 32|16 with 32|16 links");
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "precisions must be 64/64, 48/48 or 32|16 with 32|16 links");
     if (!ctx->links_loaded) return set_err(ctx, HISQ_ERR_STATE, "links not loaded");
     if (!(ctx->mass > 0)) return set_err(ctx, HISQ_ERR_STATE, "mass not set");
     HISQ_CUDA(cudaSetDevice(ctx->device));
@@ -426,6 +441,18 @@ hisq_status hisq_apply_normal_op(hisq_ctx *ctx, int precision, int link_precisio
     if (!a || !b || !t) return HISQ_ERR_OOM;
     const int lp = link_precision;
     const double m4 = 4.0 * ctx->mass * ctx->mass;
+    if (precision == HISQ_PREC_DF64) {
+        void *d = get_buf(ctx, BUF_DF_X, spinor_bytes(HISQ_PREC_DF64, Vh));
+        void *dt = get_buf(ctx, BUF_DF_T, spinor_bytes(HISQ_PREC_DF64, Vh));
+        if (!d || !dt) return HISQ_ERR_OOM;
+        TRY(launch_gather_parity(ctx, full, 0, 64, a));
+        TRY(launch_to_df64(ctx, (const double *)a, d));
+        TRY(launch_dslash_df(ctx, 1, d, dt));                                                        // D_oe a
+        TRY(launch_dslash_df_xpay(ctx, 0, dt, (double *)b, m4, (const double *)a, 0, nullptr, -1.0, -1)); // 4m^2 a - D_eo t
+        HISQ_CUDA(cudaMemsetAsync(full, 0, size_t(ctx->g.V) * 48, ctx->stream));
+        TRY(launch_scatter_parity(ctx, b, 64, 0, full));
+        return download_full(ctx, full, out);
+    }
     TRY(launch_gather_parity(ctx, full, 0, precision, a));
     TRY(launch_dslash(ctx, 1, precision, lp, a, t, 0, nullptr, 0, nullptr, 1.0, -1));       // t = D_oe a
     TRY(launch_dslash(ctx, 0, precision, lp, t, b, m4, a, 0, nullptr, -1.0, -1));           // b = 4m^2 a - D_eo t

@@ -57,11 +57,17 @@ static hisq_status residual_hi_b(hisq_ctx *ctx, const double *b, const double *x
     return launch_dslash(ctx, 0, 64, 64, tmp_odd, r, -m4, x, 1.0, b, 1.0, slot);
 }
 
-static hisq_status deflate_pair_b(hisq_ctx *ctx, int n, const double *b, double *r, double *x, double *t_odd, int slot)
+hisq_status residual_rel(hisq_ctx *ctx, bool df, const double *b, const double *x, double *r, double *tmp_odd,
+                         int slot);
+hisq_status odd_from_t(hisq_ctx *ctx, double m, const double *eta_o, const double *t, double *psi_o);
+hisq_status odd_residual_from_t(hisq_ctx *ctx, double m, const double *eta_o, const double *psi_o, double *t, int slot);
+
+static hisq_status deflate_pair_b(hisq_ctx *ctx, int n, bool df, const double *b, double *r, double *x, double *t_odd,
+                                  int slot)
 {
     if (n > 4096 || ctx->eig.prec != 32) { // see deflate_pair in solver.cu
         TRY(deflate_add(ctx, n, r, x));
-        return residual_hi_b(ctx, b, x, r, t_odd, slot);
+        return residual_rel(ctx, df, b, x, r, t_odd, slot);
     }
     double *eps = eig_eps_dev(ctx);
     double *c = (double *)get_buf(ctx, BUF_DEFL_C, sizeof(double) * 2 * (n > 0 ? n : 1));
@@ -173,6 +179,30 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
         st[j].full_residual = -1;
     }
     double defl_s = 0;
+    // double-float reliable updates per right-hand side; a residual that meets
+    // the target is recomputed in FP64 first, and a right-hand side whose FP64
+    // residual does not confirm it stays on FP64 residuals from then on
+    std::vector<char> use_df(k, P->precision_reliable == HISQ_PREC_DF64);
+    // tok[j]: t_hi holds D_oe x_j for the current x_j (left by an FP64
+    // residual); tval[j]: rh(j), no longer needed once j has finished, keeps
+    // that D_oe x_j for the odd reconstruction
+    std::vector<char> tok(k, 0), tval(k, 0);
+    auto keep_t = [&](int j) -> hisq_status {
+        if (!tok[j]) return HISQ_OK;
+        HISQ_CUDA(cudaMemcpyAsync(rh(j), t_hi, s64, cudaMemcpyDeviceToDevice, ctx->stream));
+        tval[j] = 1;
+        return HISQ_OK;
+    };
+    auto certify = [&](int j) -> hisq_status {
+        if (!use_df[j] || rt[j] > target[j]) return HISQ_OK;
+        TRY(residual_hi_b(ctx, y(j), xh(j), rh(j), t_hi, BS_R));
+        tok[j] = 1;
+        double r2;
+        TRY(read_slots(ctx, BS_R, 1, &r2));
+        rt[j] = std::sqrt(r2);
+        if (!(rt[j] <= target[j])) use_df[j] = 0;
+        return HISQ_OK;
+    };
 
     // (a2) sources, (a8) deflated guesses
     for (int j = 0; j < k; j++) {
@@ -214,7 +244,7 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
         } else {
             for (int j = 0; j < k; j++) {
                 double r2;
-                TRY(deflate_pair_b(ctx, n_defl, y(j), rh(j), xh(j), t_hi, BS_R));
+                TRY(deflate_pair_b(ctx, n_defl, use_df[j], y(j), rh(j), xh(j), t_hi, BS_R));
                 TRY(read_slots(ctx, BS_R, 1, &r2));
                 rt[j] = std::sqrt(r2);
             }
@@ -222,8 +252,10 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
         defl_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - d0).count();
     }
     for (int j = 0; j < k; j++) {
+        if (etanorm[j] > 0) TRY(certify(j));
         r_last[j] = r_defl[j] = r_best[j] = rn_seen[j] = rt[j];
         if (etanorm[j] == 0 || rt[j] <= target[j]) {
+            if (etanorm[j] > 0) TRY(keep_t(j));
             done[j] = 1;
             st[j].converged = 1;
             continue;
@@ -363,13 +395,15 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
             return HISQ_OK;
         };
         for (int j : upd) {
-            // reliable update of right-hand side j (FP64 true residual)
+            // reliable update of right-hand side j (FP64 or double-float true residual)
             TRY(launch_axpy_d(ctx, 1.0, xs(j), xprec, xh(j)));
-            TRY(residual_hi_b(ctx, y(j), xh(j), rh(j), t_hi, BS_R));
+            TRY(residual_rel(ctx, use_df[j], y(j), xh(j), rh(j), t_hi, BS_R));
+            tok[j] = !use_df[j];
             double r2;
             TRY(read_slots(ctx, BS_R, 1, &r2));
             if (!std::isfinite(r2)) return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite true residual");
             rt[j] = std::sqrt(r2);
+            TRY(certify(j));
             st[j].reliable_updates++;
             last_upd[j] = its[j];
             bool finish = false;
@@ -386,6 +420,7 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
                 finish = true;
             }
             if (finish) {
+                TRY(keep_t(j));
                 done[j] = 1;
                 changed = true;
                 continue;
@@ -408,7 +443,7 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
             } else {
                 for (int j : redefl) {
                     double r2;
-                    TRY(deflate_pair_b(ctx, n_defl, y(j), rh(j), xh(j), t_hi, BS_R));
+                    TRY(deflate_pair_b(ctx, n_defl, use_df[j], y(j), rh(j), xh(j), t_hi, BS_R));
                     TRY(read_slots(ctx, BS_R, 1, &r2));
                     rt[j] = std::sqrt(r2);
                 }
@@ -417,7 +452,10 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
             for (int j : redefl) {
                 r_defl[j] = rt[j];
                 st[j].redeflations++;
+                tok[j] = 0;
+                TRY(certify(j));
                 if (rt[j] <= target[j]) {
+                    TRY(keep_t(j));
                     st[j].converged = 1;
                     done[j] = 1;
                     changed = true;
@@ -443,10 +481,19 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
         double *out = psi + full * j;
         TRY(launch_gather_parity(ctx, e, 0, 64, eta_e));
         TRY(launch_gather_parity(ctx, e, 1, 64, eta_o));
-        TRY(launch_dslash(ctx, 1, 64, 64, xh(j), psi_o, 1.0 / (2.0 * m), eta_o, 0, nullptr, -1.0 / (2.0 * m), -1));
+        if (tval[j]) {
+            TRY(odd_from_t(ctx, m, eta_o, rh(j), psi_o));
+        } else {
+            TRY(launch_dslash(ctx, 1, 64, 64, xh(j), psi_o, 1.0 / (2.0 * m), eta_o, 0, nullptr, -1.0 / (2.0 * m), -1));
+        }
         if (P->compute_full_residual && etanorm[j] > 0) {
-            TRY(launch_dslash(ctx, 0, 64, 64, psi_o, rh(j), -2.0 * m, xh(j), 1.0, eta_e, -1.0, BS_RE));
-            TRY(launch_dslash(ctx, 1, 64, 64, xh(j), t_hi, -2.0 * m, psi_o, 1.0, eta_o, -1.0, BS_RO));
+            if (tval[j]) {
+                TRY(launch_dslash(ctx, 0, 64, 64, psi_o, t_hi, -2.0 * m, xh(j), 1.0, eta_e, -1.0, BS_RE));
+                TRY(odd_residual_from_t(ctx, m, eta_o, psi_o, rh(j), BS_RO));
+            } else {
+                TRY(launch_dslash(ctx, 0, 64, 64, psi_o, rh(j), -2.0 * m, xh(j), 1.0, eta_e, -1.0, BS_RE));
+                TRY(launch_dslash(ctx, 1, 64, 64, xh(j), t_hi, -2.0 * m, psi_o, 1.0, eta_o, -1.0, BS_RO));
+            }
             double rr[2];
             TRY(read_slots(ctx, BS_RE, 2, rr));
             st[j].full_residual = std::sqrt(rr[0] + rr[1]) / etanorm[j];

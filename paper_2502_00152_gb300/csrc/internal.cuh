@@ -189,9 +189,10 @@ __device__ __forceinline__ float stag_phase(int mu, const int c[4])
 //  FP32: [Vh] float4 (colours 0,1) then [Vh] float2 (colour 2)   24 B / site
 //  FP16: [Vh] uint4 = 6 halves (re,im x 3) + FP32 scale          16 B / site
 //  BF16: [3][Vh] bf16x2 (re,im), eigenvector storage only         12 B / site
+//  DF64: [3][Vh] float4 (re hi, re lo, im hi, im lo), residuals only 48 B / site
 inline size_t spinor_bytes(int prec, int Vh)
 {
-    return prec == 64 ? size_t(Vh) * 48
+    return (prec == 64 || prec == HISQ_PREC_DF64) ? size_t(Vh) * 48
                       : (prec == 32 ? size_t(Vh) * 24 : (prec == HISQ_PREC_BF16 ? size_t(Vh) * 12 : size_t(Vh) * 16));
 }
 
@@ -648,6 +649,8 @@ enum BufId : int {
     BUF_TC_D,          // expansion operands
     BUF_NET_PART,      // network weight-gradient partial sums
     BUF_GUESS,         // even part of a caller's initial guess
+    BUF_DF_X,          // double-float residual: x split into (hi, lo)
+    BUF_DF_T,          // double-float residual: odd temporary D_oe x
     BUF_COUNT
 };
 
@@ -682,6 +685,7 @@ struct hisq_ctx {
     float4 *links_f12[2] = {nullptr, nullptr}; // FP32 long, recon 12
     uint2 *links_h[2] = {nullptr, nullptr};    // FP16: fat (+ long when recon 18)
     uint2 *links_h12[2] = {nullptr, nullptr};  // FP16 long, recon 12
+    float4 *links_df[2] = {nullptr, nullptr};  // double-float split of links_d (built on first use)
 
     // reduction scratch
     double *partials = nullptr;
@@ -943,6 +947,16 @@ hisq_status launch_mrhs_p_update(hisq_ctx *ctx, int prec, void *r, void *p, int 
 hisq_status mrhs_set_identity(hisq_ctx *ctx, int k);
 hisq_status launch_mrhs_dslash_lin(hisq_ctx *ctx, int par, const void *in, void *out, double a, const void *x,
                                    double b, const void *y, double c, int k);
+
+// double-float operator (df64.cu): fields of HISQ_PREC_DF64 storage
+hisq_status ensure_df_links(hisq_ctx *ctx);
+hisq_status launch_to_df64(hisq_ctx *ctx, const double *in, void *out);        // FP64 -> (hi, lo)
+hisq_status launch_dslash_df(hisq_ctx *ctx, int out_parity, const void *in, void *out); // out = D in
+// out (FP64) = a x + b y + c D in (x, y FP64, nullable); |out|^2 -> slot if >= 0
+hisq_status launch_dslash_df_xpay(hisq_ctx *ctx, int out_parity, const void *in, double *out, double a,
+                                  const double *x, double b, const double *y, double c, int norm_slot);
+// r = b - (4m^2 - D_eo D_oe) x on even fields, |r|^2 -> slot
+hisq_status launch_residual_df(hisq_ctx *ctx, const double *b, const double *x, double *r, int slot);
 
 // link ingest (ingest.cu)
 hisq_status ingest_links(hisq_ctx *ctx, const double *fat_dev, const double *lng_dev, int recon,

@@ -2,6 +2,7 @@
 //   y_e = (M^dag eta)_e = 2m eta_e - D_eo eta_o
 //   x_e = V Lambda^-1 V^dag y_e                       (deflated guess, Eq. 4)
 //   CG on (M^dag M)_ee x_e = y_e in sloppy precision with FP64 reliable updates
+//     (or double-float ones, certified in FP64 before convergence is reported)
 //     (|r| < delta_rd |r_last|, delta_rd = 0.1) and re-deflation
 //     (|r| < delta_tr |r_defl|, delta_tr = 1e-3)
 //   psi_o = (eta_o - D_oe psi_e) / (2m)
@@ -40,6 +41,31 @@ static hisq_status residual_hi(hisq_ctx *ctx, const double *b, const double *x, 
     return launch_dslash(ctx, 0, 64, 64, tmp_odd, r, -m4, x, 1.0, b, 1.0, slot);
 }
 
+// the reliable-update residual r = b - A x in FP64 or, with df, in
+// double-float arithmetic on the FP32 units (df64.cu)
+hisq_status residual_rel(hisq_ctx *ctx, bool df, const double *b, const double *x, double *r, double *tmp_odd,
+                         int slot)
+{
+    return df ? launch_residual_df(ctx, b, x, r, slot) : residual_hi(ctx, b, x, r, tmp_odd, slot);
+}
+
+// Odd reconstruction from t = D_oe psi_e already computed in FP64 (left by the
+// last FP64 residual b - A x taken on the final x): psi_o = (eta_o - t) / (2m)
+hisq_status odd_from_t(hisq_ctx *ctx, double m, const double *eta_o, const double *t, double *psi_o)
+{
+    HISQ_CUDA(cudaMemcpyAsync(psi_o, t, spinor_bytes(64, ctx->g.Vh), cudaMemcpyDeviceToDevice, ctx->stream));
+    return launch_scale_axpby_d(ctx, 1.0 / (2.0 * m), eta_o, -1.0 / (2.0 * m), psi_o);
+}
+
+// odd part of the full residual, r_o = eta_o - 2m psi_o - D_oe psi_e, from the
+// same t, written over t; |r_o|^2 -> slot
+hisq_status odd_residual_from_t(hisq_ctx *ctx, double m, const double *eta_o, const double *psi_o, double *t, int slot)
+{
+    TRY(launch_scale_axpby_d(ctx, 1.0, eta_o, -1.0, t));
+    TRY(launch_axpy_d(ctx, -2.0 * m, psi_o, 64, t));
+    return launch_norm2(ctx, 64, t, slot);
+}
+
 // x += V Lambda^-1 V^dag r over the first n stored eigenpairs (Eq. 4)
 hisq_status deflate_add(hisq_ctx *ctx, int n, const double *r, double *x)
 {
@@ -58,14 +84,15 @@ hisq_status launch_defl_expand2(hisq_ctx *ctx, int n, int vprec, const void *V, 
 // r -= V c (Eq. 4 applied to the current residual).  The new residual follows
 // from A v_i = lambda_i v_i of the stored pairs instead of an FP64 operator
 // application; the next reliable update recomputes it exactly.  |r|^2 -> slot.
-static hisq_status deflate_pair(hisq_ctx *ctx, int n, const double *b, double *r, double *x, double *t_odd, int slot)
+static hisq_status deflate_pair(hisq_ctx *ctx, int n, bool df, const double *b, double *r, double *x, double *t_odd,
+                                int slot)
 {
     // beyond the fused kernel, or with FP16 eigenvectors (whose rounding, divided
-    // by small lambda_i, breaks A V Lambda^-1 c = V c): x update, then the FP64
-    // residual
+    // by small lambda_i, breaks A V Lambda^-1 c = V c): x update, then the
+    // reliable-update residual
     if (n > 4096 || ctx->eig.prec != 32) {
         TRY(deflate_add(ctx, n, r, x));
-        return residual_hi(ctx, b, x, r, t_odd, slot);
+        return residual_rel(ctx, df, b, x, r, t_odd, slot);
     }
     double *eps = eig_eps_dev(ctx);
     double *c = (double *)get_buf(ctx, BUF_DEFL_C, sizeof(double) * 2 * (n > 0 ? n : 1));
@@ -96,7 +123,8 @@ static hisq_status set_scalars(hisq_ctx *ctx, const HostScalars &h)
 // CG with reliable updates and re-deflation on one right-hand side.
 // b, x: FP64 even fields; x holds the initial guess on entry.
 static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const double *b, double *x, double target,
-                               int n_defl, double rn0, hisq_solve_stats *st, double *rfinal, double *defl_seconds)
+                               int n_defl, double rn0, hisq_solve_stats *st, double *rfinal, double *defl_seconds,
+                               bool *t_final)
 {
     const int Vh = ctx->g.Vh;
     const int prec = P->precision_sloppy;
@@ -111,9 +139,32 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
     if (!r_hi || !t_hi || !x_sl || !r_sl || !p || !tmp) return HISQ_ERR_OOM;
 
     double rt = rn0; // true residual norm, r_hi holds b - A x
+    // double-float reliable updates; a residual that meets the target is
+    // recomputed in FP64 first, and if FP64 does not confirm it the rest of the
+    // solve stays on FP64 residuals
+    bool use_df = P->precision_reliable == HISQ_PREC_DF64;
+    // t_hi = D_oe x for the current x (left by an FP64 residual)
+    bool t_ok = false;
+    *t_final = false;
+    auto certify = [&]() -> hisq_status {
+        if (!use_df || rt > target) return HISQ_OK;
+        TRY(residual_hi(ctx, b, x, r_hi, t_hi, SL_RHI));
+        t_ok = true;
+        double r2c = 0;
+        TRY(read_slots(ctx, SL_RHI, 1, &r2c));
+        rt = std::sqrt(r2c);
+        if (!(rt <= target)) {
+            use_df = false;
+            if (log_level() > 0) fprintf(stderr, "[hisq] FP64 residual %.4e does not confirm; FP64 from here\n", rt);
+        }
+        return HISQ_OK;
+    };
+
+    TRY(certify());
     *rfinal = rt;
     if (rt <= target) {
         st->converged = 1;
+        *t_final = t_ok;
         return HISQ_OK;
     }
     const double m4 = 4.0 * ctx->mass * ctx->mass;
@@ -218,17 +269,19 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
             retire(j + 1);
         }
         if (!update) continue;
-        // ---- reliable update: x_hi += x_sl; r_hi = b - A x_hi in FP64
+        // ---- reliable update: x_hi += x_sl; r_hi = b - A x_hi in FP64 (or double-float)
         HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
         retire(k);
         TRY(launch_axpy_d(ctx, 1.0, x_sl, xprec, x));
-        TRY(residual_hi(ctx, b, x, r_hi, t_hi, SL_RHI));
+        TRY(residual_rel(ctx, use_df, b, x, r_hi, t_hi, SL_RHI));
+        t_ok = !use_df;
         double r2 = 0;
         TRY(read_slots(ctx, SL_RHI, 1, &r2));
         if (!std::isfinite(r2)) return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite true residual");
         if (log_level() > 1)
             fprintf(stderr, "[hisq] cg it %lld: iterated |r| %.4e\n", k, rn_last_seen);
         rt = std::sqrt(r2);
+        TRY(certify());
         st->reliable_updates++;
         checked = k;
         last_update_it = k;
@@ -254,7 +307,8 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
         bool restart = rt > 10.0 * rn_last_seen;
         if (n_defl > 0 && P->delta_tr > 0 && rt < P->delta_tr * r_defl) {
             HISQ_CUDA(cudaEventRecord(d0, ctx->stream));
-            TRY(deflate_pair(ctx, n_defl, b, r_hi, x, t_hi, SL_RHI));
+            TRY(deflate_pair(ctx, n_defl, use_df, b, r_hi, x, t_hi, SL_RHI));
+            t_ok = false;
             HISQ_CUDA(cudaEventRecord(d1, ctx->stream));
             TRY(read_slots(ctx, SL_RHI, 1, &r2));
             float ms = 0;
@@ -264,6 +318,7 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
             r_defl = rt;
             st->redeflations++;
             restart = true;
+            TRY(certify());
             if (rt <= target) {
                 result = HISQ_OK;
                 break;
@@ -287,6 +342,7 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
     st->iterations = int(k);
     st->converged = result == HISQ_OK;
     *rfinal = rt;
+    *t_final = t_ok;
     return result;
 }
 
@@ -346,23 +402,33 @@ hisq_status solve_one(hisq_ctx *ctx, const hisq_solve_params *P, const double *e
     }
     if (n_defl > 0) {
         auto d0 = std::chrono::steady_clock::now();
-        TRY(deflate_pair(ctx, n_defl, y, r_hi, x, t_hi, SL_RHI));
+        TRY(deflate_pair(ctx, n_defl, P->precision_reliable == HISQ_PREC_DF64, y, r_hi, x, t_hi, SL_RHI));
         TRY(read_slots(ctx, SL_RHI, 1, &r2));
         defl_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - d0).count();
     }
 
     // (a6) CG with reliable updates
     double rfin = 0;
-    hisq_status cst = cg_reliable(ctx, P, y, x, target, n_defl, std::sqrt(r2), st, &rfin, &defl_s);
+    bool t_final = false;
+    hisq_status cst = cg_reliable(ctx, P, y, x, target, n_defl, std::sqrt(r2), st, &rfin, &defl_s, &t_final);
     if (cst != HISQ_OK && cst != HISQ_ERR_NOT_CONVERGED) return cst;
     st->even_residual = ynorm > 0 ? rfin / ynorm : 0;
 
-    // (a9) odd reconstruction psi_o = (eta_o - D_oe psi_e) / (2m)
-    TRY(launch_dslash(ctx, 1, 64, 64, x, psi_o, 1.0 / (2.0 * m), eta_o, 0, nullptr, -1.0 / (2.0 * m), -1));
+    // (a9) odd reconstruction psi_o = (eta_o - D_oe psi_e) / (2m); D_oe psi_e
+    // is reused when the last FP64 residual computed it on the final x
+    if (t_final) {
+        TRY(odd_from_t(ctx, m, eta_o, t_hi, psi_o));
+    } else {
+        TRY(launch_dslash(ctx, 1, 64, 64, x, psi_o, 1.0 / (2.0 * m), eta_o, 0, nullptr, -1.0 / (2.0 * m), -1));
+    }
     if (P->compute_full_residual) {
         // r_e = eta_e - 2m psi_e - D_eo psi_o ; r_o = eta_o - 2m psi_o - D_oe psi_e
         TRY(launch_dslash(ctx, 0, 64, 64, psi_o, r_hi, -2.0 * m, x, 1.0, eta_e, -1.0, SL_RE));
-        TRY(launch_dslash(ctx, 1, 64, 64, x, t_hi, -2.0 * m, psi_o, 1.0, eta_o, -1.0, SL_RO));
+        if (t_final) {
+            TRY(odd_residual_from_t(ctx, m, eta_o, psi_o, t_hi, SL_RO));
+        } else {
+            TRY(launch_dslash(ctx, 1, 64, 64, x, t_hi, -2.0 * m, psi_o, 1.0, eta_o, -1.0, SL_RO));
+        }
         double rr[2];
         TRY(read_slots(ctx, SL_RE, 2, rr));
         st->full_residual = std::sqrt(rr[0] + rr[1]) / etanorm;
@@ -386,6 +452,8 @@ static hisq_status check_solve_args(hisq_ctx *ctx, const hisq_solve_params *P, i
         return set_err(ctx, HISQ_ERR_INVALID_ARG, "link_precision_sloppy must be 32 or 16");
     if (!(P->tol > 0) || !(P->delta_rd > 0 && P->delta_rd < 1) || P->delta_tr < 0 || P->delta_tr >= 1)
         return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad tolerance / delta parameters");
+    if (P->precision_reliable != 64 && P->precision_reliable != HISQ_PREC_DF64)
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "precision_reliable must be 64 or HISQ_PREC_DF64 (48)");
     return HISQ_OK;
 }
 

@@ -35,6 +35,7 @@ HISQ_PREC_DOUBLE = 64
 HISQ_PREC_SINGLE = 32
 HISQ_PREC_HALF = 16
 HISQ_PREC_BF16 = 15  # eigenvector storage only
+HISQ_PREC_DF64 = 48  # double-float (FP32 hi + lo) reliable-update residuals and test operators
 
 
 class HisqError(RuntimeError):
@@ -47,7 +48,7 @@ class hisq_solve_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision_sloppy", ctypes.c_int),
                 ("link_precision_sloppy", ctypes.c_int), ("delta_rd", ctypes.c_double), ("deflate", ctypes.c_int),
                 ("n_defl", ctypes.c_int), ("delta_tr", ctypes.c_double), ("compute_full_residual", ctypes.c_int),
-                ("batch", ctypes.c_int), ("guess", ctypes.c_int)]
+                ("batch", ctypes.c_int), ("guess", ctypes.c_int), ("precision_reliable", ctypes.c_int)]
 
 
 class hisq_solve_stats(ctypes.Structure):
@@ -229,7 +230,7 @@ def hisq_set_mass(ctx: Context, m: float) -> None:
 
 def _default_link_prec(precision: int, link_precision):
     if link_precision is None:
-        return 64 if precision == 64 else 32
+        return precision if precision in (64, HISQ_PREC_DF64) else 32
     return link_precision
 
 

@@ -3,6 +3,7 @@ capture the Dslash kernels in the same launch configuration as the solve.
 
 usage: python -m paper_2502_00152_gb300.profile_dslash [--config c4] [--iters 4]
                                                       [--sloppy 16] [--recon 18] [--mrhs K]
+                                                      [--reliable 48]
 Kernel order of one call: source preparation and initial residual (three FP64
 Dslash launches), then per CG iteration the D_oe kernel, the fused D_eo + update
 kernel and the direction update.
@@ -65,6 +66,9 @@ def main():
     ap.add_argument("--tc-prec", type=int, default=32, help="eigenvector storage for --tc: 32 or 15 (BF16)")
     ap.add_argument("--mrhs", type=int, default=0, help="instead solve this many Gaussian right-hand sides together "
                                                         "(batched operator) for --iters iterations")
+    ap.add_argument("--reliable", type=int, default=64, choices=[64, 48],
+                    help="reliable-update arithmetic (48: the double-float residual kernels run once, at the "
+                         "forced final update)")
     ap.add_argument("--traffic-from", default=None, metavar="REPORT",
                     help="instead write profiles/dslash_traffic.json from an ncu report of this driver")
     ap.add_argument("--traffic-key", default="s16_r12", help="suffix of the keys written (sloppy bits, recon)")
@@ -90,7 +94,8 @@ def main():
     else:
         eta = I.gaussian_source(dims, 11, 0)
     prm = H.hisq_default_solve_params(tol=1e-14, max_iter=a.iters, precision_sloppy=a.sloppy,
-                                      compute_full_residual=0, batch=1 if a.mrhs > 1 else 0)
+                                      compute_full_residual=0, batch=1 if a.mrhs > 1 else 0,
+                                      precision_reliable=a.reliable)
     _, st, status = H.hisq_solve(ctx, eta, prm)
     print(f"{a.config} {dims}: {st[0]['iterations']} iterations, status {status}")
     if a.tc > 0:

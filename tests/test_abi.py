@@ -59,6 +59,7 @@ def test_status_strings_and_defaults(lib):
     assert lib.hisq_status_string(4) == b"not converged"
     p = hisq.hisq_default_solve_params()
     assert p.tol == 1e-10 and p.delta_rd == 0.1 and p.delta_tr == 1e-3  # Section 3 defaults
+    assert p.precision_reliable == 64  # FP64 reliable updates (Section 3)
     e = hisq.hisq_default_eig_params()
     assert e.n_ev > 0 and e.n_kr > e.n_ev
 
