@@ -12,6 +12,8 @@
 #include <cstring>
 #include <vector>
 
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace hisq {
@@ -60,6 +62,8 @@ static hisq_status residual_hi_b(hisq_ctx *ctx, const double *b, const double *x
 hisq_status residual_rel(hisq_ctx *ctx, bool df, const double *b, const double *x, double *r, double *tmp_odd,
                          int slot);
 hisq_status odd_from_t(hisq_ctx *ctx, double m, const double *eta_o, const double *t, double *psi_o);
+hisq_status launch_residual_df_batch(hisq_ctx *ctx, const std::vector<int> &ids, const char *Y, const char *X, char *Rr,
+                                     size_t s64, double *rr);
 hisq_status odd_residual_from_t(hisq_ctx *ctx, double m, const double *eta_o, const double *psi_o, double *t, int slot);
 
 static hisq_status deflate_pair_b(hisq_ctx *ctx, int n, bool df, const double *b, double *r, double *x, double *t_odd,
@@ -394,13 +398,30 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
             r_last[j] = rt[j];
             return HISQ_OK;
         };
+        // the double-float residuals of this round together (one pass over the links)
+        std::vector<int> gdf;
+        std::vector<double> r2df(k, 0.0);
+        for (int j : upd)
+            if (use_df[j]) gdf.push_back(j);
+        if (gdf.size() > 1) {
+            std::vector<double> rr(gdf.size());
+            for (int j : gdf) TRY(launch_axpy_d(ctx, 1.0, xs(j), xprec, xh(j)));
+            TRY(launch_residual_df_batch(ctx, gdf, Y, XH, RH, s64, rr.data()));
+            for (size_t q = 0; q < gdf.size(); q++) r2df[gdf[q]] = rr[q];
+        } else {
+            gdf.clear();
+        }
         for (int j : upd) {
             // reliable update of right-hand side j (FP64 or double-float true residual)
-            TRY(launch_axpy_d(ctx, 1.0, xs(j), xprec, xh(j)));
-            TRY(residual_rel(ctx, use_df[j], y(j), xh(j), rh(j), t_hi, BS_R));
-            tok[j] = !use_df[j];
             double r2;
-            TRY(read_slots(ctx, BS_R, 1, &r2));
+            if (std::find(gdf.begin(), gdf.end(), j) != gdf.end()) {
+                r2 = r2df[j];
+            } else {
+                TRY(launch_axpy_d(ctx, 1.0, xs(j), xprec, xh(j)));
+                TRY(residual_rel(ctx, use_df[j], y(j), xh(j), rh(j), t_hi, BS_R));
+                TRY(read_slots(ctx, BS_R, 1, &r2));
+            }
+            tok[j] = !use_df[j];
             if (!std::isfinite(r2)) return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite true residual");
             rt[j] = std::sqrt(r2);
             TRY(certify(j));

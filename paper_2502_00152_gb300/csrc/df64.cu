@@ -17,6 +17,8 @@
 //          im_hi, im_lo) of element k of the gathered FP64 hop matrix (the
 //          same matrices as the FP64 copy, phases and signs folded in)
 //   colour vectors: float4 [3][Vh] = (re_hi, re_lo, im_hi, im_lo)   48 B / site
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace hisq {
@@ -236,6 +238,173 @@ hisq_status launch_residual_df(hisq_ctx *ctx, const double *b, const double *x, 
     if (s == HISQ_OK) s = launch_dslash_df(ctx, 1, xd, td);
     if (s == HISQ_OK) s = launch_dslash_df_xpay(ctx, 0, td, r, -m4, x, 1.0, b, 1.0, slot);
     return s;
+}
+
+
+// ------------------------------------------------- several right-hand sides
+// The reliable updates of a batched solve that fall in the same round are
+// computed together.  A block holds one group of 32 consecutive sites and up to
+// 8 warps, warp w taking field blockIdx.y * 8 + w: the warps of a block load the
+// same link lines at about the same time, so after the first they come from L1
+// and the links (2304 B per site) leave DRAM about once per 8 fields, while
+// every warp keeps the register budget of the one-field kernel (two blocks of
+// 8 warps per SM).  The arithmetic per field is that of k_dslash_df.
+struct DFGroup {
+    int k;               // fields in the group (<= kMaxBatch)
+    int id[kMaxBatch];   // group slot -> right-hand-side index
+};
+
+struct DFBatchOut {
+    float4 *t;           // store: k double-float fields at a stride of 3 Vh float4
+    double2 *r;          // residual: r_id = b_id - m4 x_id + D t_slot at a stride of 3 Vh double2
+    const double2 *x, *b;
+    double m4;
+};
+
+constexpr int kDFWarps = 8;
+
+template <bool STORE>
+__global__ void __launch_bounds__(256, 2)
+    k_dslash_df_batch(Geom g, int par, const float4 *__restrict__ L, const float4 *__restrict__ in, DFBatchOut o,
+                      DFGroup grp, double *partials, unsigned int *ticket, double *norms)
+{
+    const int Vh = g.Vh;
+    const size_t fs = size_t(3) * Vh;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int q = blockIdx.y * (blockDim.x >> 5) + w; // field of this warp
+    const bool on = q < grp.k;                         // warp-uniform
+    double red = 0;
+    if (on) {
+        const float4 *src = in + size_t(q) * fs;
+        for (int sg = blockIdx.x; sg * 32 < Vh; sg += gridDim.x) {
+            const int cb = sg * 32 + lane;
+            if (cb >= Vh) continue;
+            int cc[4];
+            cb_coords(g, par, cb, cc);
+            const int s = full_site(g, cc);
+            AccDF acc;
+#pragma unroll
+            for (int u = 0; u < 6; u++) acc.S[u] = acc.E[u] = 0.f;
+#pragma unroll 1
+            for (int mu = 0; mu < 4; mu++) {
+#pragma unroll
+                for (int h = 0; h < 4; h++) {
+                    const int kind = h >> 1, bwd = h & 1;
+                    const int nb = nb_cb(g, cc, s, mu, (kind ? 3 : 1) * (bwd ? -1 : 1));
+                    float4 v[3];
+#pragma unroll
+                    for (int j = 0; j < 3; j++) v[j] = src[size_t(j) * Vh + nb];
+                    const float4 *wl = L + size_t(((mu * 2 + kind) * 2 + bwd) * 9) * Vh + cb;
+#pragma unroll
+                    for (int i = 0; i < 3; i++)
+#pragma unroll
+                        for (int j = 0; j < 3; j++) cmac_df(acc, i, __ldg(wl + size_t(3 * i + j) * Vh), v[j]);
+                }
+            }
+            if constexpr (STORE) {
+#pragma unroll
+                for (int u = 0; u < 3; u++) {
+                    const float2 re = df_norm(acc.S[2 * u], acc.E[2 * u]);
+                    const float2 im = df_norm(acc.S[2 * u + 1], acc.E[2 * u + 1]);
+                    o.t[size_t(q) * fs + size_t(u) * Vh + cb] = make_float4(re.x, re.y, im.x, im.y);
+                }
+            } else {
+                const size_t base = size_t(grp.id[q]) * fs + cb;
+#pragma unroll
+                for (int u = 0; u < 3; u++) {
+                    const size_t i = base + size_t(u) * Vh;
+                    const double2 xv = o.x[i], bv = o.b[i];
+                    const double re = fma(-o.m4, xv.x, bv.x) + (double(acc.S[2 * u]) + double(acc.E[2 * u]));
+                    const double im = fma(-o.m4, xv.y, bv.y) + (double(acc.S[2 * u + 1]) + double(acc.E[2 * u + 1]));
+                    o.r[i] = make_double2(re, im);
+                    red += re * re + im * im;
+                }
+            }
+        }
+    }
+    if constexpr (!STORE) {
+        // per-field sums: lanes by a fixed shuffle tree, blocks in block order
+        __shared__ bool am_last;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) red += __shfl_down_sync(0xffffffffu, red, off);
+        if (lane == 0 && on) partials[size_t(blockIdx.x) * kMaxBatch + q] = red;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) am_last = (atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1);
+        __syncthreads();
+        if (!am_last) return;
+        __threadfence();
+        for (int f = threadIdx.x; f < grp.k; f += blockDim.x) {
+            double t = 0;
+            for (int b = 0; b < (int)gridDim.x; b++) t += ((volatile double *)partials)[size_t(b) * kMaxBatch + f];
+            norms[grp.id[f]] = t;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            *ticket = 0u;
+            __threadfence();
+        }
+    }
+}
+
+static hisq_status run_df_batch(hisq_ctx *ctx, const DFGroup &grp, const float4 *xd, float4 *td, const DFBatchOut &o)
+{
+    const int Vh = ctx->g.Vh;
+    const int wpb = std::min(grp.k, kDFWarps);
+    const int ny = (grp.k + wpb - 1) / wpb;
+    auto go = [&](auto kern, int par, const float4 *in) -> hisq_status {
+        static int bps = -1;
+        if (bps < 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 256, 0) != cudaSuccess || bps < 1))
+            bps = 1;
+        // all ny field chunks resident together (blocks of fewer warps fit
+        // proportionally more per SM), so that the chunks sweep the sites in
+        // step and re-read each link line from L2 rather than DRAM
+        ctx->launches++;
+        const long resident = long(ctx->num_sms) * bps * (kDFWarps / wpb);
+        long gx = std::min(long((Vh + 31) / 32), std::max(1L, resident / ny));
+        gx = std::min(gx, long(ctx->max_red_blocks));
+        dim3 grid(unsigned(gx), unsigned(ny), 1u);
+        kern<<<grid, 32 * wpb, 0, ctx->stream>>>(ctx->g, par, ctx->links_df[par], in, o, grp, ctx->bpartials,
+                                                 ctx->ticket + 48, ctx->bscal->out);
+        const cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? HISQ_OK : cuda_err(ctx, e, "batched double-float dslash launch");
+    };
+    hisq_status st = go(k_dslash_df_batch<true>, 1, xd);
+    if (st == HISQ_OK) st = go(k_dslash_df_batch<false>, 0, td);
+    return st;
+}
+
+// r_j = y_j - (4m^2 - D_eo D_oe) x_j for the right-hand sides `ids` of a batched
+// solve (FP64 fields at a stride of s64 bytes from Y, X, Rr); |r_j|^2 -> rr[q]
+hisq_status launch_residual_df_batch(hisq_ctx *ctx, const std::vector<int> &ids, const char *Y, const char *X, char *Rr,
+                                     size_t s64, double *rr)
+{
+    const int Vh = ctx->g.Vh;
+    const size_t sdf = spinor_bytes(HISQ_PREC_DF64, Vh);
+    hisq_status st = ensure_df_links(ctx);
+    if (st != HISQ_OK) return st;
+    double out[kMaxBatch];
+    for (size_t q0 = 0; q0 < ids.size(); q0 += kMaxBatch) {
+        const int k = int(std::min(ids.size() - q0, size_t(kMaxBatch)));
+        char *xd = (char *)get_buf(ctx, BUF_DF_X, sdf * k);
+        char *td = (char *)get_buf(ctx, BUF_DF_T, sdf * k);
+        if (!xd || !td) return HISQ_ERR_OOM;
+        DFGroup grp;
+        grp.k = k;
+        for (int q = 0; q < k; q++) {
+            grp.id[q] = ids[q0 + q];
+            st = launch_to_df64(ctx, (const double *)(X + s64 * grp.id[q]), xd + sdf * q);
+            if (st != HISQ_OK) return st;
+        }
+        DFBatchOut o{(float4 *)td, (double2 *)Rr, (const double2 *)X, (const double2 *)Y,
+                     4.0 * ctx->mass * ctx->mass};
+        st = run_df_batch(ctx, grp, (const float4 *)xd, (float4 *)td, o);
+        if (st != HISQ_OK) return st;
+        HISQ_CUDA(cudaMemcpyAsync(out, ctx->bscal->out, sizeof out, cudaMemcpyDeviceToHost, ctx->stream));
+        HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+        for (int q = 0; q < k; q++) rr[q0 + q] = out[grp.id[q]];
+    }
+    return HISQ_OK;
 }
 
 } // namespace hisq

@@ -133,3 +133,27 @@ def test_df64_full_size_solve_true_residual():
         assert st[0]["reliable_updates"] >= 5
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("nrhs", [2, 3, 6, 9])
+def test_df64_batched_residuals_match_oracle(nrhs):
+    """A batched solve stopped by max_iter takes one reliable update of every
+    right-hand side in the same round: the double-float residuals of the whole
+    group come from one batched launch pair (1, 2, 3 or 4 fields per thread and
+    ragged warps).  The reported even residual |y_e - A psi_e| / |y_e| matches
+    the oracle's FP64 residual of the returned psi_e."""
+    dims, m = (6, 6, 6, 8), 0.02
+    ctx, o = make(dims, seed=5, eps=0.3, mass=m)
+    try:
+        etas = np.stack([I.gaussian_source(dims, 13, j) for j in range(nrhs)])
+        for rp in (64, DF):
+            prm = H.hisq_default_solve_params(batch=1, max_iter=3, tol=1e-14, precision_sloppy=32,
+                                              precision_reliable=rp, compute_full_residual=0)
+            psi, st, status = H.hisq_solve(ctx, etas, prm)
+            assert status == H.HISQ_ERR_NOT_CONVERGED
+            for j in range(nrhs):
+                y = project_parity(dims, o.prepare_source(m, etas[j]), 0)
+                ref = o.even_residual(m, project_parity(dims, psi[j], 0), y)
+                assert abs(st[j]["even_residual"] - ref) <= 1e-9 * ref, (rp, j, st[j]["even_residual"], ref)
+    finally:
+        ctx.close()
