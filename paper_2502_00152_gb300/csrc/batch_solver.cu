@@ -191,20 +191,38 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
     // residual); tval[j]: rh(j), no longer needed once j has finished, keeps
     // that D_oe x_j for the odd reconstruction
     std::vector<char> tok(k, 0), tval(k, 0);
+    // |r_e|^2 of the full residual left by the FP64 confirmation of j (-1: none)
+    std::vector<double> re2f(k, -1.0);
     auto keep_t = [&](int j) -> hisq_status {
         if (!tok[j]) return HISQ_OK;
         HISQ_CUDA(cudaMemcpyAsync(rh(j), t_hi, s64, cudaMemcpyDeviceToDevice, ctx->stream));
         tval[j] = 1;
         return HISQ_OK;
     };
+    // the FP64 confirmation is the even part of the full residual (see
+    // cg_reliable in solver.cu): t = D_oe x_j, psi_o = (eta_o - t) / 2m,
+    // r_e = eta_e - 2m x_j - D_eo psi_o, y_j - A x_j = 2m r_e
     auto certify = [&](int j) -> hisq_status {
         if (!use_df[j] || rt[j] > target[j]) return HISQ_OK;
-        TRY(residual_hi_b(ctx, y(j), xh(j), rh(j), t_hi, BS_R));
+        const double *e = eta + full * j;
+        TRY(launch_gather_parity(ctx, e, 0, 64, eta_e));
+        TRY(launch_gather_parity(ctx, e, 1, 64, eta_o));
+        TRY(launch_dslash(ctx, 1, 64, 64, xh(j), t_hi, 0, nullptr, 0, nullptr, 1.0, -1));
+        TRY(odd_from_t(ctx, m, eta_o, t_hi, psi_o));
+        TRY(launch_dslash(ctx, 0, 64, 64, psi_o, rh(j), -2.0 * m, xh(j), 1.0, eta_e, -1.0, BS_R));
+        double re2;
+        TRY(read_slots(ctx, BS_R, 1, &re2));
+        rt[j] = 2.0 * m * std::sqrt(re2);
         tok[j] = 1;
-        double r2;
-        TRY(read_slots(ctx, BS_R, 1, &r2));
-        rt[j] = std::sqrt(r2);
-        if (!(rt[j] <= target[j])) use_df[j] = 0;
+        re2f[j] = re2;
+        if (!(rt[j] <= target[j])) {
+            // not confirmed: rh(j) = 2m r_e = y_j - A x_j, FP64 residuals from here
+            HISQ_CUDA(cudaMemcpyAsync(t_hi, rh(j), s64, cudaMemcpyDeviceToDevice, ctx->stream));
+            TRY(launch_scale_axpby_d(ctx, 0.0, t_hi, 2.0 * m, rh(j)));
+            tok[j] = 0;
+            re2f[j] = -1;
+            use_df[j] = 0;
+        }
         return HISQ_OK;
     };
 
@@ -508,15 +526,22 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
             TRY(launch_dslash(ctx, 1, 64, 64, xh(j), psi_o, 1.0 / (2.0 * m), eta_o, 0, nullptr, -1.0 / (2.0 * m), -1));
         }
         if (P->compute_full_residual && etanorm[j] > 0) {
+            double rr[2] = {re2f[j], 0.0};
             if (tval[j]) {
-                TRY(launch_dslash(ctx, 0, 64, 64, psi_o, t_hi, -2.0 * m, xh(j), 1.0, eta_e, -1.0, BS_RE));
+                // an FP64 confirmation of this x_j has already formed |r_e|^2
+                if (re2f[j] < 0)
+                    TRY(launch_dslash(ctx, 0, 64, 64, psi_o, t_hi, -2.0 * m, xh(j), 1.0, eta_e, -1.0, BS_RE));
                 TRY(odd_residual_from_t(ctx, m, eta_o, psi_o, rh(j), BS_RO));
             } else {
+                re2f[j] = -1;
                 TRY(launch_dslash(ctx, 0, 64, 64, psi_o, rh(j), -2.0 * m, xh(j), 1.0, eta_e, -1.0, BS_RE));
                 TRY(launch_dslash(ctx, 1, 64, 64, xh(j), t_hi, -2.0 * m, psi_o, 1.0, eta_o, -1.0, BS_RO));
             }
-            double rr[2];
-            TRY(read_slots(ctx, BS_RE, 2, rr));
+            if (re2f[j] < 0) {
+                TRY(read_slots(ctx, BS_RE, 2, rr));
+            } else {
+                TRY(read_slots(ctx, BS_RO, 1, &rr[1]));
+            }
             st[j].full_residual = std::sqrt(rr[0] + rr[1]) / etanorm[j];
         } else if (etanorm[j] == 0) {
             st[j].full_residual = 0;

@@ -122,10 +122,17 @@ static hisq_status set_scalars(hisq_ctx *ctx, const HostScalars &h)
 
 // CG with reliable updates and re-deflation on one right-hand side.
 // b, x: FP64 even fields; x holds the initial guess on entry.
+// With double-float reliable updates the FP64 confirmation of a converged
+// residual is the even part of the full residual: t = D_oe x,
+// psi_o = (eta_o - t) / 2m, r_e = eta_e - 2m x - D_eo psi_o, and y - A x = 2m r_e
+// (exact reconstruction), so it also leaves psi_o and |r_e|^2 (*re2_final >= 0)
+// for the caller.
 static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const double *b, double *x, double target,
                                int n_defl, double rn0, hisq_solve_stats *st, double *rfinal, double *defl_seconds,
-                               bool *t_final)
+                               bool *t_final, const double *eta_e, const double *eta_o, double *psi_o,
+                               double *re2_final)
 {
+    const double m = ctx->mass;
     const int Vh = ctx->g.Vh;
     const int prec = P->precision_sloppy;
     const int lprec = prec == 64 ? 64 : P->link_precision_sloppy;
@@ -145,15 +152,26 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
     bool use_df = P->precision_reliable == HISQ_PREC_DF64;
     // t_hi = D_oe x for the current x (left by an FP64 residual)
     bool t_ok = false;
+    // psi_o and |r_e|^2 of the full residual for the current x (left by a confirmation)
+    bool fin_ok = false;
+    double re2_fin = -1;
     *t_final = false;
+    *re2_final = -1;
     auto certify = [&]() -> hisq_status {
         if (!use_df || rt > target) return HISQ_OK;
-        TRY(residual_hi(ctx, b, x, r_hi, t_hi, SL_RHI));
-        t_ok = true;
-        double r2c = 0;
-        TRY(read_slots(ctx, SL_RHI, 1, &r2c));
-        rt = std::sqrt(r2c);
+        TRY(launch_dslash(ctx, 1, 64, 64, x, t_hi, 0, nullptr, 0, nullptr, 1.0, -1));
+        TRY(odd_from_t(ctx, m, eta_o, t_hi, psi_o));
+        TRY(launch_dslash(ctx, 0, 64, 64, psi_o, r_hi, -2.0 * m, x, 1.0, eta_e, -1.0, SL_RHI));
+        double re2 = 0;
+        TRY(read_slots(ctx, SL_RHI, 1, &re2));
+        rt = 2.0 * m * std::sqrt(re2);
+        t_ok = fin_ok = true;
+        re2_fin = re2;
         if (!(rt <= target)) {
+            // not confirmed: r_hi = 2m r_e = b - A x, and FP64 residuals from here
+            HISQ_CUDA(cudaMemcpyAsync(t_hi, r_hi, spinor_bytes(64, Vh), cudaMemcpyDeviceToDevice, ctx->stream));
+            TRY(launch_scale_axpby_d(ctx, 0.0, t_hi, 2.0 * m, r_hi));
+            t_ok = fin_ok = false;
             use_df = false;
             if (log_level() > 0) fprintf(stderr, "[hisq] FP64 residual %.4e does not confirm; FP64 from here\n", rt);
         }
@@ -165,6 +183,7 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
     if (rt <= target) {
         st->converged = 1;
         *t_final = t_ok;
+        *re2_final = fin_ok ? re2_fin : -1;
         return HISQ_OK;
     }
     const double m4 = 4.0 * ctx->mass * ctx->mass;
@@ -275,6 +294,7 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
         TRY(launch_axpy_d(ctx, 1.0, x_sl, xprec, x));
         TRY(residual_rel(ctx, use_df, b, x, r_hi, t_hi, SL_RHI));
         t_ok = !use_df;
+        fin_ok = false;
         double r2 = 0;
         TRY(read_slots(ctx, SL_RHI, 1, &r2));
         if (!std::isfinite(r2)) return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite true residual");
@@ -308,7 +328,7 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
         if (n_defl > 0 && P->delta_tr > 0 && rt < P->delta_tr * r_defl) {
             HISQ_CUDA(cudaEventRecord(d0, ctx->stream));
             TRY(deflate_pair(ctx, n_defl, use_df, b, r_hi, x, t_hi, SL_RHI));
-            t_ok = false;
+            t_ok = fin_ok = false;
             HISQ_CUDA(cudaEventRecord(d1, ctx->stream));
             TRY(read_slots(ctx, SL_RHI, 1, &r2));
             float ms = 0;
@@ -343,6 +363,7 @@ static hisq_status cg_reliable(hisq_ctx *ctx, const hisq_solve_params *P, const 
     st->converged = result == HISQ_OK;
     *rfinal = rt;
     *t_final = t_ok;
+    *re2_final = fin_ok ? re2_fin : -1;
     return result;
 }
 
@@ -410,28 +431,37 @@ hisq_status solve_one(hisq_ctx *ctx, const hisq_solve_params *P, const double *e
     // (a6) CG with reliable updates
     double rfin = 0;
     bool t_final = false;
-    hisq_status cst = cg_reliable(ctx, P, y, x, target, n_defl, std::sqrt(r2), st, &rfin, &defl_s, &t_final);
+    double re2_final = -1;
+    hisq_status cst = cg_reliable(ctx, P, y, x, target, n_defl, std::sqrt(r2), st, &rfin, &defl_s, &t_final, eta_e,
+                                  eta_o, psi_o, &re2_final);
     if (cst != HISQ_OK && cst != HISQ_ERR_NOT_CONVERGED) return cst;
     st->even_residual = ynorm > 0 ? rfin / ynorm : 0;
 
     // (a9) odd reconstruction psi_o = (eta_o - D_oe psi_e) / (2m); D_oe psi_e
-    // is reused when the last FP64 residual computed it on the final x
-    if (t_final) {
+    // is reused when the last FP64 residual computed it on the final x, and
+    // an FP64 confirmation has already formed psi_o and r_e
+    const bool fin = re2_final >= 0;
+    if (fin) {
+        // psi_o is in place
+    } else if (t_final) {
         TRY(odd_from_t(ctx, m, eta_o, t_hi, psi_o));
     } else {
         TRY(launch_dslash(ctx, 1, 64, 64, x, psi_o, 1.0 / (2.0 * m), eta_o, 0, nullptr, -1.0 / (2.0 * m), -1));
     }
     if (P->compute_full_residual) {
         // r_e = eta_e - 2m psi_e - D_eo psi_o ; r_o = eta_o - 2m psi_o - D_oe psi_e
-        TRY(launch_dslash(ctx, 0, 64, 64, psi_o, r_hi, -2.0 * m, x, 1.0, eta_e, -1.0, SL_RE));
+        double re2 = re2_final, ro2 = 0;
+        if (!fin) {
+            TRY(launch_dslash(ctx, 0, 64, 64, psi_o, r_hi, -2.0 * m, x, 1.0, eta_e, -1.0, SL_RE));
+            TRY(read_slots(ctx, SL_RE, 1, &re2));
+        }
         if (t_final) {
             TRY(odd_residual_from_t(ctx, m, eta_o, psi_o, t_hi, SL_RO));
         } else {
             TRY(launch_dslash(ctx, 1, 64, 64, x, t_hi, -2.0 * m, psi_o, 1.0, eta_o, -1.0, SL_RO));
         }
-        double rr[2];
-        TRY(read_slots(ctx, SL_RE, 2, rr));
-        st->full_residual = std::sqrt(rr[0] + rr[1]) / etanorm;
+        TRY(read_slots(ctx, SL_RO, 1, &ro2));
+        st->full_residual = std::sqrt(re2 + ro2) / etanorm;
     }
     TRY(launch_scatter_parity(ctx, x, 64, 0, psi));
     TRY(launch_scatter_parity(ctx, psi_o, 64, 1, psi));
