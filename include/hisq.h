@@ -102,14 +102,18 @@ typedef struct {
                                 meets the tolerance is recomputed in FP64 before
                                 convergence is reported, and the rest of that
                                 right-hand side's solve uses FP64 if it is not
-                                confirmed).  The double-float links take as much
-                                device memory as the FP64 copy (2304 B per site). */
+                                confirmed; that FP64 check is the even part of the
+                                full residual, 2m r_e = y_e - A psi_e).  The
+                                double-float links are built on first use and take
+                                as much device memory as the FP64 copy (2304 B per
+                                site); HISQ_ERR_OOM if they do not fit.  Default 64. */
 } hisq_solve_params;
 
 /* Per right-hand-side results of a solve. */
 typedef struct {
     int iterations;          /* sloppy CG iterations                               */
-    int reliable_updates;    /* FP64 true-residual recomputations                  */
+    int reliable_updates;    /* true-residual recomputations (in the arithmetic of
+                                precision_reliable)                                */
     int redeflations;        /* deflations after the initial guess                 */
     int converged;           /* 1 if the tolerance was met                         */
     double even_residual;    /* |y_e - A psi_e| / |y_e|, FP64                      */

@@ -183,13 +183,16 @@ hisq_status ensure_df_links(hisq_ctx *ctx)
     if (ctx->links_df[0]) return HISQ_OK;
     if (!ctx->links_loaded) return set_err(ctx, HISQ_ERR_STATE, "links not loaded");
     const size_t n = size_t(ctx->g.Vh) * 16 * 9;
-    for (int p = 0; p < 2; p++) {
-        ctx->links_df[p] = (float4 *)dev_alloc(ctx, n * sizeof(float4));
-        if (!ctx->links_df[p])
-            return set_err(ctx, HISQ_ERR_OOM, "double-float links (%.1f GB)", 2.0 * n * sizeof(float4) / 1e9);
-        const hisq_status s = launch_split(ctx, n, ctx->links_d[p], ctx->links_df[p]);
-        if (s != HISQ_OK) return s;
+    float4 *d[2] = {(float4 *)dev_alloc(ctx, n * sizeof(float4)), nullptr};
+    if (d[0]) d[1] = (float4 *)dev_alloc(ctx, n * sizeof(float4));
+    hisq_status s = (d[0] && d[1]) ? HISQ_OK : HISQ_ERR_OOM;
+    for (int p = 0; p < 2 && s == HISQ_OK; p++) s = launch_split(ctx, n, ctx->links_d[p], d[p]);
+    if (s != HISQ_OK) { // neither parity is kept, so the next call starts over (message set by the failing call)
+        for (int p = 0; p < 2; p++) dev_free(ctx, d[p], d[p] ? n * sizeof(float4) : 0);
+        return s;
     }
+    ctx->links_df[0] = d[0];
+    ctx->links_df[1] = d[1];
     return HISQ_OK;
 }
 

@@ -157,3 +157,27 @@ def test_df64_batched_residuals_match_oracle(nrhs):
                 assert abs(st[j]["even_residual"] - ref) <= 1e-9 * ref, (rp, j, st[j]["even_residual"], ref)
     finally:
         ctx.close()
+
+
+def test_df64_link_allocation_failure_leaves_no_half_built_state():
+    """The double-float links are built on first use.  Refused allocations
+    (host-side injection) of the first parity, then of the second, give
+    HISQ_ERR_OOM and keep neither; the next call builds both and applies the
+    operator to the parity tolerance."""
+    dims = (6, 6, 6, 6)
+    ctx, o = make(dims)
+    try:
+        src = I.gaussian_field(dims, 23)
+        ref = dslash_ref(o, dims, src, 0)
+        assert rel(H.hisq_apply_dslash(ctx, 0, 64, src), ref) <= 1e-13  # scratch fields exist from here
+        # 1st: the double-float scratch field is allocated, the first link parity refused
+        # 2nd: the scratch field exists, the first parity is allocated, the second refused
+        for _ in range(2):
+            H.hisq_inject_alloc_failure(ctx, 1)
+            with pytest.raises(H.HisqError):
+                H.hisq_apply_dslash(ctx, 0, DF, src)
+        H.hisq_inject_alloc_failure(ctx, -1)
+        assert rel(H.hisq_apply_dslash(ctx, 0, DF, src), ref) <= TOL_DF
+        assert rel(H.hisq_apply_dslash(ctx, 1, DF, src), dslash_ref(o, dims, src, 1)) <= TOL_DF
+    finally:
+        ctx.close()
