@@ -228,6 +228,26 @@ def test_prepare_source_is_even_part_of_Mdag_eta():
     assert np.linalg.norm(y - ref) <= 1e-14 * np.linalg.norm(ref)
 
 
+def test_full_residual_after_reconstruction_is_schur_residual():
+    """With the odd sites reconstructed exactly, psi_o = (eta_o - D_oe psi_e) / 2m
+    (Section 2), the odd rows of eta - M psi vanish for ANY psi_e and the even
+    rows equal (y_e - A_ee psi_e) / 2m: a wrong sign of the hop term, a wrong
+    mass factor or a wrong reconstruction breaks one of the two.  (The solver's
+    FP64 confirmation forms the even-system residual this way.)"""
+    dims = (6, 4, 6, 4)
+    o = Oracle(dims, *_rand_links(dims, seed=11))
+    m = 0.07
+    eta = I.gaussian_field(dims, 21)
+    psi_e = project_parity(dims, I.gaussian_field(dims, 22), 0)
+    psi = o.reconstruct(m, psi_e, eta)
+    assert np.array_equal(project_parity(dims, psi, 0), psi_e)
+    r = eta - o.apply_M(m, psi)
+    assert np.linalg.norm(project_parity(dims, r, 1)) <= 1e-13 * np.linalg.norm(eta)
+    schur = project_parity(dims, o.prepare_source(m, eta) - o.apply_Aee(m, psi_e), 0) / (2 * m)
+    re = project_parity(dims, r, 0)
+    assert np.linalg.norm(re - schur) <= 1e-12 * np.linalg.norm(schur)
+
+
 # ---------------------------------------------------------- eigenpairs
 def test_lanczos_matches_dense():
     """Plain Lanczos with full reorthogonalisation finds the same lowest
