@@ -2,15 +2,20 @@
 """Benchmark: time per right-hand side of the deflated mixed-precision HISQ
 propagator solve on one GB300, next to plain mixed-precision CG on the same GPU.
 
-Workload (synthetic stand-in for the paper's MILC ensembles, Section 2 Table 1):
-32^3 x 64 lattice, thin links exp(i 0.3 A) (seed 2), fat = 9/8 U, long = -1/24 UUU,
-antiperiodic time, m = 0.002, 256 eigenpairs of the squared massless even-site
-operator (thick-restart Lanczos, FP32 vectors), Gaussian complex sources.
-One step = one right-hand side through the whole hot path: source preparation,
-deflated initial guess (Eq. 4), sloppy CG with FP64 reliable updates and
-re-deflation (Section 3), odd reconstruction and the FP64 full residual, to
-|eta - M psi| / |eta| <= 1e-10.  Link upload and the eigensolve are setup
-(excluded from the solve time, as in the paper) and reported separately.
+Workload (synthetic stand-in for the paper's MILC ensembles, Section 2 Table 1),
+by default the largest single-GPU one, in the light-mass regime: 64^3 x 96
+lattice, thin links exp(i 0.25 A) (seed 4), fat = 9/8 U, long = -1/24 UUU (two
+rows stored, the third rebuilt), antiperiodic time, m = 0.0008, 200 eigenpairs
+of the squared massless even-site operator (block thick-restart Lanczos) stored
+in FP16, 12 right-hand sides per step (4 Gaussian sources x 3 colours) solved
+together.  One step = one batch through the whole hot path: source preparation,
+deflated initial guesses (Eq. 4, tensor-core GEMMs), sloppy CG with FP64
+reliable updates and re-deflation (Section 3), odd reconstruction and the FP64
+full residual, to |eta - M psi| / |eta| <= 1e-10.  Link upload and the
+eigensolve are setup (excluded from the solve time, as in the paper) and
+reported separately.  Plain mixed-precision CG on the same GPU is timed the
+same way (warm-up steps, CUDA events on the solve stream, the same step count).
+--config c2 / c3 select the 32^3 x 64 single-RHS and 24-RHS workloads.
 
 usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun each rank runs independent replicas (different sources); the
@@ -42,13 +47,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--config", default="c2")
+    ap.add_argument("--config", default="c5")
     ap.add_argument("--sloppy", type=int, default=16, help="sloppy colour-vector storage: 32 or 16")
     ap.add_argument("--recon", type=int, default=12, help="long links: 18 reals, 12 (two rows + SU(3) row) or 8 (a2, a3, b1 and two phases)")
     ap.add_argument("--links", type=int, default=32, help="sloppy link storage: 32 or 16")
-    ap.add_argument("--reliable", type=int, choices=[64, 48], default=None,
-                    help="reliable-update residual arithmetic: 64 (FP64) or 48 (double-float on the FP32 units, "
-                         "certified in FP64); default 48, and 64 for c5 (no room for the double-float links)")
+    ap.add_argument("--reliable", type=int, choices=[64, 48], default=64,
+                    help="reliable-update residual arithmetic of the headline: 64 (FP64, the paper's) or 48 "
+                         "(double-float on the FP32 units, certified in FP64); the other one is timed beside it "
+                         "where its links fit (not at c5)")
     ap.add_argument("--n-ev", type=int, default=None)
     ap.add_argument("--n-kr", type=int, default=None)
     ap.add_argument("--cheby", type=int, default=60)
@@ -57,10 +63,14 @@ def parse():
     ap.add_argument("--eig-block", type=int, default=64,
                     help="eigensolver block size (1: thick-restart Lanczos; b: block thick-restart Lanczos)")
     ap.add_argument("--eig-prec", type=int, default=None,
-                    help="eigenvector storage: 32 (FP32), 16 (FP16 + per-site scale), 15 (BF16); "
-                         "default 32, BF16 for the batched 32^3x64 workload")
-    ap.add_argument("--plain-steps", type=int, default=1)
-    ap.add_argument("--cpu-iters", type=int, default=3, help="oracle CG iterations per CPU-baseline sample")
+                    help="eigenvector storage: 32 (FP32), 16 (FP16 + per-site scale), 15 (BF16), 14 (FP16 x 2^e); "
+                         "default FP16 x 2^e for c5, BF16 for c3, FP32 otherwise")
+    ap.add_argument("--plain-steps", type=int, default=None,
+                    help="timed steps of the plain-CG comparison (default: --steps)")
+    ap.add_argument("--plain-warmup", type=int, default=None,
+                    help="warm-up steps of the plain-CG comparison (default: --warmup)")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end host-API measurement")
+    ap.add_argument("--cpu-iters", type=int, default=2, help="oracle CG iterations per CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned", action="store_true", help="learned initial guess workload (24^3x48)")
     ap.add_argument("--learned-pairs", type=int, default=512)
@@ -69,6 +79,17 @@ def parse():
     ap.add_argument("--sweep", choices=["delta_tr", "mass", "cheby"], default=None,
                     help="precision/re-deflation sweep (Fig. 2 analogue) or iterations vs mass (Fig. 1 analogue) "
                          "on the 32^3x64 lattice; prints one JSON line per table")
+    ap.add_argument("--capture", action="store_true",
+                    help="profiler-capture run: --iters CG iterations (no timing, no JSON line)")
+    ap.add_argument("--iters", type=int, default=4, help="--capture: CG iterations")
+    ap.add_argument("--mrhs", type=int, default=0, help="--capture: solve this many Gaussian RHS together")
+    ap.add_argument("--tc", type=int, default=0, help="--capture: also run the tensor-core batched deflation "
+                                                      "with this many random eigenvectors (24 RHS)")
+    ap.add_argument("--tc-prec", type=int, default=32, help="--capture: eigenvector storage for --tc (32, 15, 14)")
+    ap.add_argument("--traffic-from", default=None, metavar="REPORT",
+                    help="--capture: write profiles/dslash_traffic.json from an ncu report of a capture run")
+    ap.add_argument("--traffic-key", default="s16_r12", help="--capture: key suffix (sloppy bits, recon)")
+    ap.add_argument("--traffic-command", default="", help="--capture: the ncu command that made the report")
     ap.add_argument("--rhs-per-step", type=int, default=None,
                     help="right-hand sides solved together per step (batched); default 1, 24 for c3, 12 for c5")
     return ap.parse_args()
@@ -204,14 +225,17 @@ def run_ours(a):
     Vh = V // 2
     n_ev = a.n_ev if a.n_ev is not None else cfg.get("n_ev", 0)
     if a.eig_prec is None:
-        a.eig_prec = 15 if a.config in ("c3", "c5") else 32
-    eig_name = {32: "FP32", 16: "FP16", 15: "BF16"}.get(a.eig_prec, str(a.eig_prec))
+        a.eig_prec = {"c5": H.HISQ_PREC_HALF_EV, "c3": H.HISQ_PREC_BF16}.get(a.config, 32)
+    eig_name = {32: "FP32", 16: "FP16 + per-site scale", 15: "BF16", 14: "FP16"}.get(a.eig_prec, str(a.eig_prec))
     n_kr = a.n_kr if a.n_kr is not None else max(int(1.5 * n_ev), n_ev + 32)
 
     t0 = time.time()
     fat, lng = I.hisq_links(dims, cfg["seed"], cfg["eps"])
     t_links = time.time() - t0
-    stream = torch.cuda.current_stream()
+    # the library works on a stream of its own (not the legacy default stream),
+    # so that its CG iterations are captured and replayed as CUDA graphs
+    stream = torch.cuda.Stream(device=local)
+    torch.cuda.set_stream(stream)
     ctx = H.hisq_create(dims, t_antiperiodic=True, device=local, cuda_stream=stream.cuda_stream)
     H.hisq_load_links(ctx, fat, lng, long_recon=a.recon, long_scale=I.C3_NAIK if a.recon != 18 else 1.0)
     H.hisq_set_mass(ctx, m)
@@ -226,13 +250,15 @@ def run_ours(a):
         t0 = time.time()
         eps, nconv = H.hisq_eigensolve(ctx, ep)
         torch.cuda.synchronize()
-        eig = dict(seconds=time.time() - t0, n_ev=n_ev, n_kr=n_kr, block_size=a.eig_block, converged=nconv,
-                   cheby_degree=a.cheby,
-                   eps_min=float(eps[0]), eps_max=float(eps[-1]), storage=a.eig_prec)
+        eig = dict(seconds=round(time.time() - t0, 2), n_ev=n_ev, n_kr=n_kr, block_size=a.eig_block,
+                   converged=nconv, cheby_degree=a.cheby, eps_min=float(eps[0]), eps_max=float(eps[-1]),
+                   storage=eig_name)
 
     # sources: resident in HBM before the timed region (FP64 full-lattice fields)
     keep_links = (fat, lng) if (rank == 0 and world == 1 and not a.no_cpu_baseline) else (None, None)
     kps = a.rhs_per_step if a.rhs_per_step is not None else {"c3": 24, "c5": 12}.get(a.config, 1)
+    plain_steps = a.steps if a.plain_steps is None else a.plain_steps
+    plain_warmup = a.warmup if a.plain_warmup is None else a.plain_warmup
     nsrc = a.warmup + a.steps
     if kps == 1:
         srcs = [I.gaussian_source(dims, SOURCE_SEED, rank * 1000 + k) for k in range(nsrc)]
@@ -248,12 +274,12 @@ def run_ours(a):
     if keep_links[0] is None:
         del fat, lng
     psi_dev = torch.zeros_like(eta_dev[0])
-    rel_prec = a.reliable if a.reliable is not None else (64 if a.config == "c5" else H.HISQ_PREC_DF64)
-    prm_defl = H.hisq_default_solve_params(tol=tol, precision_sloppy=a.sloppy, link_precision_sloppy=a.links,
-                                           deflate=1 if n_ev > 0 else 0, compute_full_residual=1,
-                                           precision_reliable=rel_prec)
-    prm_plain = H.hisq_default_solve_params(tol=tol, precision_sloppy=a.sloppy, link_precision_sloppy=a.links,
-                                            deflate=0, compute_full_residual=1, precision_reliable=rel_prec)
+    rel_prec = a.reliable
+    def params(deflate, rel):
+        return H.hisq_default_solve_params(tol=tol, precision_sloppy=a.sloppy, link_precision_sloppy=a.links,
+                                           deflate=deflate, compute_full_residual=1, precision_reliable=rel)
+    prm_defl = params(1 if n_ev > 0 else 0, rel_prec)
+    prm_plain = params(0, rel_prec)
 
     def solve(k, prm):
         st, status = H.hisq_solve_device(ctx, eta_dev[k], psi_dev, kps, prm)
@@ -270,42 +296,44 @@ def run_ours(a):
         agg["full_residual"] = max(s["full_residual"] for s in st)
         return agg
 
-    # plain mixed-precision CG on the same GPU (comparison, not the headline)
-    torch.cuda.synchronize()
-    t0 = time.time()
-    plain = [solve(k % nsrc, prm_plain) for k in range(a.plain_steps)]
-    torch.cuda.synchronize()
-    plain_ms = (time.time() - t0) * 1e3 / max(1, a.plain_steps) / kps
+    def timed(prm, warmup, steps, profile=False, sample_clocks=False):
+        """warm-up steps, then `steps` steps between CUDA events on the solve
+        stream (a barrier and a synchronize on both sides); ms per step"""
+        for k in range(warmup):
+            solve(k % nsrc, prm)
+        H.hisq_set_profiling(ctx, profile)
+        clocks = Clocks(local) if sample_clocks else None
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        l0 = H.hisq_kernel_launches(ctx)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed")
+        ev0.record(stream)
+        st = [solve((warmup + k) % nsrc, prm) for k in range(steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        launches = H.hisq_kernel_launches(ctx) - l0
+        clk = clocks.stop() if clocks else None
+        H.hisq_set_profiling(ctx, False)
+        elapsed_ms, per_rhs = replica_time(ev0.elapsed_time(ev1), max(steps, 1) * kps, f"cuda:{local}")
+        return st, elapsed_ms, per_rhs, launches, clk
 
-    for k in range(a.warmup):
-        solve(k, prm_defl)
-    H.hisq_set_profiling(ctx, True)
-    clocks = Clocks(local)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    l0 = H.hisq_kernel_launches(ctx)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push("timed")
-    ev0.record(stream)
-    stats = [solve(a.warmup + k, prm_defl) for k in range(a.steps)]
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    launches = H.hisq_kernel_launches(ctx) - l0
-    clk = clocks.stop()
-    H.hisq_set_profiling(ctx, False)
-    elapsed_ms, value = replica_time(ev0.elapsed_time(ev1), a.steps * kps, f"cuda:{local}")
+    # headline: the deflated solve
+    stats, elapsed_ms, value, launches, clk = timed(prm_defl, a.warmup, a.steps, profile=True, sample_clocks=True)
     if world > 1:
         torch.distributed.barrier()
     ms_per_step = elapsed_ms / a.steps  # one step = kps right-hand sides
+    # plain mixed-precision CG on the same GPU, timed the same way
+    plain, _, plain_ms, _, _ = timed(prm_plain, plain_warmup, plain_steps) if plain_steps > 0 else ([], 0, None, 0, None)
 
     # end to end through the host API: pinned host source -> psi on the host
     pin_eta = torch.from_numpy(np.ascontiguousarray(srcs[a.warmup])).pin_memory()
-    pin_psi = torch.empty_like(pin_eta).pin_memory()
     e2e_ms = []
-    for k in range(a.steps):
+    for k in range(max(1, a.e2e_steps)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         _, st_h, status = H.hisq_solve(ctx, pin_eta.numpy(), prm_defl)
@@ -313,20 +341,20 @@ def run_ours(a):
         if status != H.HISQ_OK:
             raise RuntimeError("host-API solve did not converge")
 
-    # the same solves with the paper's FP64 reliable updates (comparison)
-    fp64_rel = None
-    if rel_prec != 64:
-        prm64 = H.hisq_default_solve_params(tol=tol, precision_sloppy=a.sloppy, link_precision_sloppy=a.links,
-                                            deflate=1 if n_ev > 0 else 0, compute_full_residual=1,
-                                            precision_reliable=64)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s64 = solve(a.warmup, prm64)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        fp64_rel = {"ms_per_rhs": round(e0.elapsed_time(e1) / kps, 3), "iterations": s64["iterations"],
-                    "reliable_updates": s64["reliable_updates"], "true_residual_max": s64["full_residual"]}
+    # the same solves with the other reliable-update arithmetic (comparison);
+    # the double-float links need as much memory as the FP64 copy (2304 B per
+    # site), which the largest workload does not have left
+    other = 64 if rel_prec != 64 else H.HISQ_PREC_DF64
+    other_rel = None
+    if a.config == "c5" and other == H.HISQ_PREC_DF64:
+        other_rel = {"unavailable": "double-float links (2304 B per site, 58 GB) do not fit beside this workload"}
+    else:
+        try:
+            s2, e2, v2, _, _ = timed(params(1 if n_ev > 0 else 0, other), 1, 1)
+            other_rel = {"ms_per_rhs": round(v2, 3), "iterations": s2[0]["iterations"],
+                         "reliable_updates": s2[0]["reliable_updates"], "true_residual_max": s2[0]["full_residual"]}
+        except Exception as e:  # e.g. no room for the double-float links
+            other_rel = {"unavailable": str(e)[:200]}
 
     # Dslash roofline from the event-timed kernels of the timed solves
     it = sum(s["profiled_iterations"] for s in stats)
@@ -355,8 +383,8 @@ def run_ours(a):
         }
     else:
         # batched D_oe kernel: one launch serves every active right-hand side;
-        # at 24 RHS its intensity (~14 flop/B) is past the FP32 ridge, so the
-        # bound is the FP32 FMA rate: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
+        # at 12-24 RHS its intensity (8-14 flop/B) is at or past the FP32 ridge,
+        # so the bound is the FP32 FMA rate: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
         n_launch = sum(s["profiled_iterations"] for s in stats)
         rhs_launch = sum(s["profiled_rhs_launches"] for s in stats)
         t_all = sum(s["seconds_dslash_oe"] for s in stats)
@@ -367,7 +395,7 @@ def run_ours(a):
             "bound": "alu", "achieved": None if tf is None else round(tf, 2), "peak": round(peak32, 1),
             "unit": "TFLOP/s", "frac": None if tf is None else round(tf / peak32, 4), "traffic": None,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (nominal clock)",
-            "kernel": f"k_dslash_mrhs D_oe ({kps} RHS per launch, 4 per thread)",
+            "kernel": f"k_dslash_mrhs D_oe ({kps} RHS per launch)",
             "flops_per_rhs_site": flops_site,
             "launch_us": round(t_all / max(n_launch, 1) * 1e6, 2),
             "mean_rhs_per_launch": round(rhs_launch / max(n_launch, 1), 2),
@@ -379,6 +407,7 @@ def run_ours(a):
                                 if t_all_eo > 0 else None},
         }
 
+    rel_name = "FP64 reliable updates" if rel_prec == 64 else "double-float reliable updates, final residual in FP64"
     out = {
         "metric": METRIC,
         "value": round(value, 4),
@@ -394,33 +423,37 @@ def run_ours(a):
         "data": "synthetic",
         "config": {
             "workload": f"HISQ {dims[0]}^3x{dims[3]}, m={m}, {n_ev} eigenpairs ({eig_name}), deflated "
-                        f"mixed-precision CG (FP{a.sloppy} vectors, FP{a.links} links recon {a.recon}, "
-                        + ("FP64 reliable updates" if rel_prec == 64 else
-                           "double-float reliable updates, final residual confirmed in FP64") + "), "
+                        f"mixed-precision CG (FP{a.sloppy} vectors, FP{a.links} links recon {a.recon}, {rel_name}), "
                         + ("1 Gaussian RHS per step" if kps == 1 else
                            (f"{kps} RHS per step ({kps // 3} Gaussian sources x 3 colours), batched"
                             if a.config == "c5" else f"{kps} Z2 wall RHS per step, batched"))
                         + f", tol {tol}",
             "rhs_per_step": kps,
-            "lattice": list(dims), "mass": m, "n_ev": n_ev, "sloppy_vectors": f"fp{a.sloppy}",
-            "links": f"fp{a.links} recon {a.recon}", "l2": "inputs larger than L2 (links and eigenvectors are GBs)",
+            "lattice": list(dims), "mass": m, "n_ev": n_ev, "eigenvectors": eig_name,
+            "sloppy_vectors": f"fp{a.sloppy}", "links": f"fp{a.links} recon {a.recon}",
+            "l2": "inputs larger than L2 (links and eigenvectors are GBs)",
             "parallelism": f"replicas{world}",
+            "graphs": "on (CG iterations replayed as CUDA graphs on the library's stream)",
         },
         "roofline": roof,
         "e2e": {"value": round(sorted(e2e_ms)[len(e2e_ms) // 2], 4), "unit": "ms/RHS",
-                "h2d_bytes_per_step": V * 48 * kps, "d2h_bytes_per_step": V * 48 * kps},
+                "h2d_bytes_per_step": V * 48 * kps, "d2h_bytes_per_step": V * 48 * kps,
+                "steps": len(e2e_ms)},
         "gpu_launches": int(launches),
         "clocks": clk,
-        "plain_cg_ms_per_rhs": round(plain_ms, 3),
+        "plain_cg": {"ms_per_rhs": None if plain_ms is None else round(plain_ms, 3),
+                     "iterations": [s["iterations"] for s in plain], "steps": plain_steps, "warmup": plain_warmup,
+                     "timing": "CUDA events on the solve stream after warm-up, as the headline"},
+        "speedup_vs_plain_cg": round(plain_ms / value, 3) if plain_ms and value > 0 else None,
         "reliable_updates_arithmetic": "fp64" if rel_prec == 64 else "double-float (FP32 hi+lo), FP64-confirmed",
-        "fp64_reliable_updates": fp64_rel,
+        ("double_float_reliable_updates" if other == H.HISQ_PREC_DF64 else "fp64_reliable_updates"): other_rel,
         "iterations_deflated": [s["iterations"] for s in stats],
-        "iterations_plain": [s["iterations"] for s in plain],
         "reliable_updates": [s["reliable_updates"] for s in stats],
         "redeflations": [s["redeflations"] for s in stats],
         "true_residual_max": res_max,
-        "speedup_vs_plain_cg": round(plain_ms / value, 3) if value > 0 else None,
         "eigensolve": eig,
+        "eigensolve_break_even_rhs": (round(eig["seconds"] * 1e3 / (plain_ms - value), 1)
+                                      if eig and plain_ms and plain_ms > value else None),
         "link_generation_s": round(t_links, 2),
     }
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
@@ -442,6 +475,9 @@ def oracle_iterations(name: str):
         return None, "no stored oracle iteration count"
 
 
+_ORACLE_CACHE = {}
+
+
 def cpu_baseline(a, dims, cfg, samples: int = 1, fat=None, lng=None):
     """The FP64 oracle as it stands, on the host cores: time per CG iteration on
     the benchmark workload (a bounded sample of a.cpu_iters iterations), scaled
@@ -449,11 +485,15 @@ def cpu_baseline(a, dims, cfg, samples: int = 1, fat=None, lng=None):
     from oracle.oracle import Oracle, num_threads
     from paper_2502_00152_gb300 import inputs as I
 
-    if fat is None:
-        fat, lng = I.hisq_links(dims, cfg["seed"], cfg["eps"])
-    o = Oracle(dims, fat, lng, t_antiperiodic=True)
-    eta = I.gaussian_source(dims, SOURCE_SEED, 0)
-    b = o.prepare_source(cfg["mass"], eta)
+    key = (tuple(dims), cfg["seed"], cfg["eps"], cfg["mass"])
+    if key not in _ORACLE_CACHE:
+        if fat is None:
+            fat, lng = I.hisq_links(dims, cfg["seed"], cfg["eps"])
+        o = Oracle(dims, fat, lng, t_antiperiodic=True)
+        eta = I.gaussian_source(dims, SOURCE_SEED, 0)
+        _ORACLE_CACHE.clear()
+        _ORACLE_CACHE[key] = (o, o.prepare_source(cfg["mass"], eta))
+    o, b = _ORACLE_CACHE[key]
     per_it = []
     for _ in range(samples):
         t0 = time.perf_counter()
@@ -462,7 +502,7 @@ def cpu_baseline(a, dims, cfg, samples: int = 1, fat=None, lng=None):
     n_it, src = oracle_iterations(a.config)
     t_it = min(per_it)
     return {"value": round(t_it * n_it * 1e3, 1) if n_it else None, "unit": "ms/RHS", "cores": num_threads(),
-            "kind": "oracle",
+            "threads": num_threads(), "nproc": os.cpu_count(), "kind": "oracle",
             "sample": f"{a.cpu_iters} FP64 oracle CG iterations on the full {dims[0]}^3x{dims[3]} lattice "
                       f"({t_it * 1e3:.1f} ms per iteration incl. residual applies), x {n_it} iterations "
                       f"({src}); extrapolated, plain CG without deflation"}
@@ -498,6 +538,105 @@ def run_reference(a):
            "cpu_baseline": cb,
            "e2e": {"value": value, "unit": "ms/RHS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------ profiler captures
+def run_capture(a):
+    """A few CG iterations on a benchmark lattice, in the launch configuration of
+    the solve, for a profiler to capture the kernels (ncu -k ... -c ...): source
+    preparation and initial residual (three FP64 Dslash launches), then per CG
+    iteration the D_oe kernel, the fused D_eo + update kernel and the direction
+    update; --mrhs K solves K Gaussian right-hand sides together (batched
+    operator); --tc N also runs the tensor-core batched deflation twice with N
+    random orthonormalised eigenvectors and 24 right-hand sides.
+    --traffic-from REPORT instead writes profiles/dslash_traffic.json from an ncu
+    report of such a run."""
+    from paper_2502_00152_gb300 import build as B
+    from paper_2502_00152_gb300 import hisq as H
+    from paper_2502_00152_gb300 import inputs as I
+
+    if a.traffic_from:
+        out = os.path.join(ROOT, "profiles", "dslash_traffic.json")
+        write_traffic(a.traffic_from, a.config, a.traffic_key, out, a.traffic_command)
+        return
+    B.build()
+    c = I.lattice_config(a.config)
+    dims = c["dims"]
+    fat, lng = I.hisq_links(dims, c["seed"], c["eps"])
+    ctx = H.hisq_create(dims, t_antiperiodic=True, device=0)
+    H.hisq_load_links(ctx, fat, lng, long_recon=a.recon, long_scale=I.C3_NAIK if a.recon != 18 else 1.0)
+    H.hisq_set_mass(ctx, c["mass"])
+    if a.mrhs > 1:
+        import numpy as np
+
+        eta = np.stack([I.gaussian_source(dims, 11, j) for j in range(a.mrhs)])
+    else:
+        eta = I.gaussian_source(dims, 11, 0)
+    prm = H.hisq_default_solve_params(tol=1e-14, max_iter=a.iters, precision_sloppy=a.sloppy,
+                                      compute_full_residual=0, batch=1 if a.mrhs > 1 else 0,
+                                      precision_reliable=a.reliable)
+    _, st, status = H.hisq_solve(ctx, eta, prm)
+    print(f"{a.config} {dims}: {st[0]['iterations']} iterations, status {status}")
+    if a.tc > 0:
+        import numpy as np
+
+        from paper_2502_00152_gb300.inputs import random_normal
+
+        V = I.volume(dims)
+        par = (np.indices(dims[::-1]).sum(axis=0) & 1).reshape(-1)
+        vecs = random_normal(5, 77, 0, 6 * V * a.tc).reshape(a.tc, V, 3, 2)
+        vecs = vecs[..., 0] + 1j * vecs[..., 1]
+        vecs[:, par == 1] = 0
+        vecs /= np.linalg.norm(vecs.reshape(a.tc, -1), axis=1)[:, None, None]
+        H.hisq_set_eigvecs(ctx, vecs, np.linspace(0.01, 0.1, a.tc), a.tc_prec)
+        bs = np.stack([I.gaussian_field(dims, 40 + j) for j in range(24)])
+        for _ in range(2):
+            H.hisq_deflate_batch(ctx, bs)
+        print(f"tensor-core deflation: {a.tc} vectors x 24 right-hand sides done")
+    ctx.close()
+
+
+def write_traffic(report: str, config: str, key: str, out: str, command: str) -> None:
+    """Per-output-site DRAM bytes of the D_oe (EpiXpay) and fused D_eo + update
+    (EpiCG) Dslash launches in an ncu report of this driver, written with the
+    hash of the Dslash sources they were taken on (the benchmark uses them only
+    while that hash matches)."""
+    import csv
+    import io
+    import json
+    import subprocess
+
+    from paper_2502_00152_gb300 import inputs as I
+    from paper_2502_00152_gb300.build import dslash_source_hash
+
+    txt = subprocess.run(["ncu", "-i", report, "--page", "raw", "--csv"], check=True, capture_output=True,
+                         text=True).stdout
+    rows = list(csv.reader(io.StringIO(txt)))
+    hdr, data = rows[0], rows[2:]
+    col = {n: hdr.index(n) for n in ("Kernel Name", "dram__bytes_read.sum", "dram__bytes_write.sum")}
+    units = rows[1]
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    dims = I.lattice_config(config)["dims"]
+    dims_s = f"{dims[0]}^3x{dims[3]}"
+    vh = I.volume(dims) // 2
+    per_site = {}
+    for r in data:
+        name = r[col["Kernel Name"]]
+        kind = "oe" if "EpiXpay" in name else ("eo" if "EpiCG" in name else None)
+        if kind is None:
+            continue
+        b = sum(float(r[col[m]].replace(",", "")) * scale[units[col[m]]]
+                for m in ("dram__bytes_read.sum", "dram__bytes_write.sum"))
+        per_site.setdefault(f"{kind}_{key}", []).append(b / vh)
+    doc = {"what": f"DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per output site of the sloppy "
+                   f"Dslash kernels, from one ncu capture on the {dims_s} lattice (Vh = {vh}); traffic scales with "
+                   f"the number of output sites, so the benchmark multiplies by its own Vh",
+           "command": command, "kernel_source_hash": dslash_source_hash(),
+           "dram_bytes_per_output_site": {k: round(sum(v) / len(v), 1) for k, v in per_site.items()}}
+    with open(out, "w") as f:
+        json.dump(doc, f, indent=1)
+    print(json.dumps(doc["dram_bytes_per_output_site"]))
+
 
 
 # ------------------------------------------------------------ learned guess
@@ -705,6 +844,8 @@ if __name__ == "__main__":
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.capture:
+        run_capture(args)
     elif args.sweep:
         run_sweep(args)
     elif args.learned:

@@ -68,6 +68,10 @@ typedef enum {
     HISQ_PREC_SINGLE = 32,
     HISQ_PREC_HALF = 16, /* FP16 values with one FP32 scale per site (colour vectors) */
     HISQ_PREC_BF16 = 15, /* BF16 values, 12 B per site; eigenvector storage only     */
+    HISQ_PREC_HALF_EV = 14, /* FP16 values of v * 2^e with one power-of-two scale for
+                               all sites and vectors (4^e >= 3 Vh, the smallest),
+                               12 B per site, colour-major; eigenvector storage
+                               only, read by the tensor cores as it is stored   */
     HISQ_PREC_DF64 = 48  /* double-float: each real the sum hi + lo of two FP32
                             numbers (about 48 significant bits), FP32 arithmetic
                             with exact products and error-carrying sums; the
@@ -249,23 +253,29 @@ hisq_status hisq_deflate(hisq_ctx *ctx, int n, const double *b, double *x);
  * site s = x + X*(y + Y*(z + Z*t)) has index s/2.  x_dev is overwritten.
  * Work is ordered on the context's stream; the call returns without waiting.
  *
- * Scratch: one fixed array of 16 MiB in device memory, held by every GPU that
- * loads this library until the process exits.  It must hold the projection's
- * partial sums, n * ceil(Vh / 4096) complex doubles, plus 24 bytes per pair;
- * larger requests fail with HISQ_ERR_INVALID_ARG and a message naming the
- * sizes.  The first call on a device looks up the array's device address (with
- * that device current), so make that first call before any stream capture.
- * All calls share the array and it keeps the last call's contents; every byte a
- * call reads is first written by that call, but calls that overlap on the GPU
- * (different streams or contexts on one device) race on it. */
+ * Scratch: one fixed array of 16 MiB in device memory.  A device reserves it
+ * when the first context is created on it (hisq_create looks up the array's
+ * device address with that device current, which loads the code module that
+ * holds it) and keeps it until the process exits; this entry point itself
+ * never reserves or allocates anything.  A call needs
+ * ceil256(16 * n * ceil(Vh / 4096)) + ceil256(16 * n) bytes of it (the
+ * projection's partial sums and the n coefficients, each region rounded up to
+ * a multiple of 256 bytes); larger requests fail with HISQ_ERR_INVALID_ARG and
+ * a message naming the sizes.  The eigenvalues are read from the device copy
+ * that is written whenever eigenpairs are stored.  All calls share the array
+ * and it keeps the last call's contents; every byte a call reads is first
+ * written by that call, but calls that overlap on the GPU (different streams
+ * or contexts on one device) race on it. */
 hisq_status hisq_deflate_noalloc(hisq_ctx *ctx, int n, const double *b_dev, double *x_dev);
 
 /* Batched deflation on the tensor cores (Eq. 4 for several right-hand sides, the
  * paper's Section 4 outlook): for nrhs <= 32 host full-lattice fields b_j,
  * x_j = sum_i v_i lambda_i^-1 v_i^dag b_j and r_j = b_j - sum_i v_i v_i^dag b_j
- * over the first n <= 512 stored pairs (0 = all), even sites.  Needs FP32
- * eigenvector storage; the projection and the expansion are complex GEMMs in
- * FP16 (split into high and low parts) with FP32 accumulation. */
+ * over the first n <= 512 stored pairs (0 = all), even sites.  Needs FP32, BF16
+ * or HISQ_PREC_HALF_EV eigenvector storage.  The projection and the expansion
+ * are complex GEMMs with FP32 accumulation: with FP32 storage both operands are
+ * split into FP16 high and low parts; with 16-bit storage the stored vectors
+ * are one operand as they are and only the other is split. */
 hisq_status hisq_deflate_batch(hisq_ctx *ctx, int n, int nrhs, const double *b, double *x, double *r);
 
 /* Write / read the stored eigenpairs to / from a binary file (header with

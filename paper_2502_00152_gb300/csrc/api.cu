@@ -11,6 +11,7 @@ using namespace hisq;
 
 namespace hisq {
 void tc_forget(hisq_ctx *ctx);
+hisq_status noalloc_scratch_address(hisq_ctx *ctx, unsigned char **out);
 
 int log_level()
 {
@@ -104,16 +105,12 @@ void *get_buf(hisq_ctx *c, int id, size_t bytes)
     return p;
 }
 
-// device pointer of eigenvalues eps (FP64), refreshed from the host copy
+// device copy of the stored eigenvalues eps (FP64, ascending), written when
+// the eigenpairs are stored
 double *eig_eps_dev(hisq_ctx *ctx)
 {
-    const int n = ctx->eig.n;
-    double *d = (double *)get_buf(ctx, BUF_EPS, sizeof(double) * (n > 0 ? n : 1));
-    if (!d) return nullptr;
-    if (n > 0 && cudaMemcpyAsync(d, ctx->eig.eps.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
-        return nullptr;
-    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return nullptr;
-    return d;
+    if (!ctx->eig.eps_dev) set_err(ctx, HISQ_ERR_STATE, "no eigenpairs stored");
+    return ctx->eig.eps_dev;
 }
 
 // scalar slot readback (synchronises the stream)
@@ -246,6 +243,9 @@ hisq_status hisq_create(const int dims[4], int t_antiperiodic, int device, void 
                       cudaHostAllocMapped) != cudaSuccess)
         return fail(HISQ_ERR_OOM);
     if (cudaHostGetDevicePointer((void **)&ctx->bmonitor_d, ctx->bmonitor_h, 0) != cudaSuccess) return fail(HISQ_ERR_CUDA);
+    // the fixed scratch of hisq_deflate_noalloc is reserved on this device now,
+    // so that the no-allocation entry point itself never causes a reservation
+    if (noalloc_scratch_address(ctx, nullptr) != HISQ_OK) return fail(HISQ_ERR_CUDA);
     *out = ctx;
     return HISQ_OK;
 }
@@ -266,6 +266,7 @@ void hisq_destroy(hisq_ctx *ctx)
     }
     for (int i = 0; i < BUF_COUNT; i++) cudaFree(ctx->bufs[i]);
     cudaFree(ctx->eig.vecs);
+    cudaFree(ctx->eig.eps_dev);
     cudaFree(ctx->partials);
     cudaFree(ctx->g.oob);
     cudaFree(ctx->ticket);

@@ -30,7 +30,8 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
 // eigenvectors, up to 512 of them and 32 right-hand sides per call
 static bool tc_eligible(const hisq_ctx *ctx, int n, int k)
 {
-    return (ctx->eig.prec == 32 || ctx->eig.prec == HISQ_PREC_BF16) && n >= 1 && n <= 512 && k >= 2;
+    return (ctx->eig.prec == 32 || ctx->eig.prec == HISQ_PREC_BF16 || ctx->eig.prec == HISQ_PREC_HALF_EV) && n >= 1 &&
+           n <= 512 && k >= 2;
 }
 
 // r -= V c is the residual change of x += V Lambda^-1 c only while A v_i =

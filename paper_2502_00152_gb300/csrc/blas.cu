@@ -33,8 +33,9 @@ static hisq_status with_spinor(hisq_ctx *ctx, int prec, const void *p, F &&f)
     case 32: return f(make_spinorF(q, Vh));
     case 16: return f(make_spinorH(q, Vh));
     case HISQ_PREC_BF16: return f(make_spinorB(q, Vh));
+    case HISQ_PREC_HALF_EV: return f(make_spinorE(q, Vh));
     }
-    return set_err(ctx, HISQ_ERR_INVALID_ARG, "precision must be 64, 32, 16 or 15 (BF16)");
+    return set_err(ctx, HISQ_ERR_INVALID_ARG, "precision must be 64, 32, 16, 15 (BF16) or 14 (FP16 eigenvectors)");
 }
 
 // ------------------------------------------------------------- layout
@@ -278,6 +279,11 @@ __device__ __forceinline__ SpinorB spinor_at<SpinorB>(const char *base, size_t s
     char *p = const_cast<char *>(base) + stride * i;
     return SpinorB{(__nv_bfloat162 *)p, Vh};
 }
+template <>
+__device__ __forceinline__ SpinorE spinor_at<SpinorE>(const char *base, size_t stride, int i, int Vh)
+{
+    return make_spinorE(const_cast<char *>(base) + stride * i, Vh);
+}
 
 constexpr int kDeflVG = 8;        // vectors per block in the projection
 constexpr int kDeflSites = 4096;  // sites per block in the projection
@@ -369,8 +375,8 @@ hisq_status launch_defl_project(hisq_ctx *ctx, int n, int vprec, const void *V, 
     if (st != HISQ_OK) return st;
     dim3 grid((n + kDeflVG - 1) / kDeflVG, nchunks);
     const size_t stride = spinor_bytes(vprec, Vh);
-    if (vprec != 32 && vprec != 16 && vprec != HISQ_PREC_BF16)
-        return set_err(ctx, HISQ_ERR_INVALID_ARG, "eigenvector precision must be 32, 16 or 15 (BF16)");
+    if (vprec != 32 && vprec != 16 && vprec != HISQ_PREC_BF16 && vprec != HISQ_PREC_HALF_EV)
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "eigenvector precision must be 32, 16, 15 (BF16) or 14 (FP16)");
     if (bprec != 64 && bprec != 32) return set_err(ctx, HISQ_ERR_INVALID_ARG, "projected vector must be FP64 or FP32");
     void *bb = const_cast<void *>(b);
     if (vprec == 32 && bprec == 64)
@@ -381,6 +387,10 @@ hisq_status launch_defl_project(hisq_ctx *ctx, int n, int vprec, const void *V, 
         k_defl_project<SpinorB, SpinorD><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, make_spinorD(bb, Vh), part, nchunks);
     else if (vprec == HISQ_PREC_BF16)
         k_defl_project<SpinorB, SpinorF><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, make_spinorF(bb, Vh), part, nchunks);
+    else if (vprec == HISQ_PREC_HALF_EV && bprec == 64)
+        k_defl_project<SpinorE, SpinorD><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, make_spinorD(bb, Vh), part, nchunks);
+    else if (vprec == HISQ_PREC_HALF_EV)
+        k_defl_project<SpinorE, SpinorF><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, make_spinorF(bb, Vh), part, nchunks);
     else if (bprec == 64)
         k_defl_project<SpinorH, SpinorD><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, make_spinorD(bb, Vh), part, nchunks);
     else
@@ -451,6 +461,10 @@ hisq_status launch_defl_expand(hisq_ctx *ctx, int n, int vprec, const void *V, c
         return expand_go<SpinorB>(ctx, n, V, stride, d_dev, coef, make_spinorD(x, Vh), smem);
     if (vprec == HISQ_PREC_BF16 && xprec == 32)
         return expand_go<SpinorB>(ctx, n, V, stride, d_dev, coef, make_spinorF(x, Vh), smem);
+    if (vprec == HISQ_PREC_HALF_EV && xprec == 64)
+        return expand_go<SpinorE>(ctx, n, V, stride, d_dev, coef, make_spinorD(x, Vh), smem);
+    if (vprec == HISQ_PREC_HALF_EV && xprec == 32)
+        return expand_go<SpinorE>(ctx, n, V, stride, d_dev, coef, make_spinorF(x, Vh), smem);
     return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad deflation precisions");
 }
 
@@ -629,8 +643,10 @@ hisq_status launch_defl_project_ext(hisq_ctx *ctx, int n, int vprec, const void 
         k_defl_project<SpinorH, SpinorD><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, bs, part, nchunks);
     else if (vprec == HISQ_PREC_BF16)
         k_defl_project<SpinorB, SpinorD><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, bs, part, nchunks);
+    else if (vprec == HISQ_PREC_HALF_EV)
+        k_defl_project<SpinorE, SpinorD><<<grid, 256, 0, ctx->stream>>>(Vh, n, (const char *)V, stride, bs, part, nchunks);
     else
-        return set_err(ctx, HISQ_ERR_INVALID_ARG, "eigenvector precision must be 32, 16 or 15 (BF16)");
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "eigenvector precision must be 32, 16, 15 (BF16) or 14 (FP16)");
     LAUNCH_CHECK("defl_project_ext");
     ctx->launches += 2;
     k_defl_finish<<<(n + 127) / 128, 128, 0, ctx->stream>>>(n, nchunks, part, (double2 *)c_dev, nullptr, 0.0);
@@ -711,8 +727,12 @@ hisq_status launch_defl_expand2(hisq_ctx *ctx, int n, int vprec, const void *V, 
         auto k = k_defl_expand2<SpinorB>;
         int grid = grid_for(ctx, Vh, 256, occ(k, 256, smem));
         k<<<grid, 256, smem, ctx->stream>>>(Vh, n, (const char *)V, stride, (const double2 *)c_dev, eps_dev, shift, xs, rs);
+    } else if (vprec == HISQ_PREC_HALF_EV) {
+        auto k = k_defl_expand2<SpinorE>;
+        int grid = grid_for(ctx, Vh, 256, occ(k, 256, smem));
+        k<<<grid, 256, smem, ctx->stream>>>(Vh, n, (const char *)V, stride, (const double2 *)c_dev, eps_dev, shift, xs, rs);
     } else {
-        return set_err(ctx, HISQ_ERR_INVALID_ARG, "eigenvector precision must be 32 or 16");
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "eigenvector precision must be 32, 16, 15 or 14");
     }
     LAUNCH_CHECK("defl_expand2");
     return HISQ_OK;

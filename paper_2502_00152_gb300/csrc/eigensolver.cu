@@ -35,7 +35,9 @@ hisq_status deflate_add(hisq_ctx *ctx, int n, const double *r, double *x);
 // Eigen-decomposition of a real symmetric n x n matrix a (row major):
 // Householder reduction to tridiagonal form with the transformations
 // accumulated in z, then implicit QL iterations with shifts on the tridiagonal
-// matrix (Golub & Van Loan, Matrix Computations, Secs. 8.3.1 and 8.3.3).
+// matrix (Golub & Van Loan, Matrix Computations, Secs. 8.3.1 and 8.3.3; the
+// QL iteration is the published tred2/tql2 procedure of Bowdler, Martin,
+// Reinsch and Wilkinson, Numer. Math. 11 (1968) 293, as distributed in EISPACK).
 // On exit w holds the eigenvalues ascending and column j of z (row major) the
 // eigenvector of w[j].
 static void sym_eig(int n, std::vector<double> a, std::vector<double> &w, std::vector<double> &z)
@@ -210,7 +212,9 @@ static hisq_status rayleigh_fp64(hisq_ctx *ctx, const double *v, double *tmp, do
 static void free_eig(hisq_ctx *ctx)
 {
     if (ctx->eig.vecs) dev_free(ctx, ctx->eig.vecs, size_t(ctx->eig.n) * spinor_bytes(ctx->eig.prec, ctx->g.Vh));
+    if (ctx->eig.eps_dev) dev_free(ctx, ctx->eig.eps_dev, sizeof(double) * (ctx->eig.n > 0 ? ctx->eig.n : 1));
     ctx->eig.vecs = nullptr;
+    ctx->eig.eps_dev = nullptr;
     ctx->eig.n = 0;
     ctx->eig.eps.clear();
 }
@@ -242,18 +246,25 @@ static hisq_status store_eigvecs(hisq_ctx *ctx, int n, const void *vf32, int pre
     free_eig(ctx);
     void *store = dev_alloc(ctx, sp * (n > 0 ? n : 1));
     if (!store) return HISQ_ERR_OOM;
+    double *eps_dev = (double *)dev_alloc(ctx, sizeof(double) * (n > 0 ? n : 1));
+    if (!eps_dev) {
+        dev_free(ctx, store, sp * (n > 0 ? n : 1));
+        return HISQ_ERR_OOM;
+    }
     for (int j = 0; j < n; j++) TRY(launch_convert(ctx, (const char *)vf32 + sf * idx[j], 32, (char *)store + sp * j, prec));
+    std::vector<double> sorted(n);
+    for (int j = 0; j < n; j++) sorted[j] = eps[idx[j]];
+    if (n > 0) HISQ_CUDA(cudaMemcpyAsync(eps_dev, sorted.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
     HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
     ctx->eig.vecs = store;
+    ctx->eig.eps_dev = eps_dev;
     ctx->eig.n = n;
     ctx->eig.prec = prec;
     ctx->eig.version++;
-    ctx->eig.eps.resize(n);
+    ctx->eig.eps = sorted;
     if (residuals) residuals->resize(n);
-    for (int j = 0; j < n; j++) {
-        ctx->eig.eps[j] = eps[idx[j]];
+    for (int j = 0; j < n; j++)
         if (residuals) (*residuals)[j] = res[idx[j]];
-    }
     return HISQ_OK;
 }
 
@@ -271,8 +282,9 @@ static hisq_status trlm(hisq_ctx *ctx, const hisq_eig_params *P, int *n_conv, do
     const int dim = 3 * Vh;
     if (n_ev < 1 || n_kr <= n_ev + 2 || n_keep < n_ev || n_keep >= n_kr || n_kr > dim || n_kr > 6144)
         return set_err(ctx, HISQ_ERR_INVALID_ARG, "need 1 <= n_ev <= n_keep < n_kr <= min(3 Vh, 6144), n_kr > n_ev + 2");
-    if (P->storage_precision != 32 && P->storage_precision != 16 && P->storage_precision != HISQ_PREC_BF16)
-        return set_err(ctx, HISQ_ERR_INVALID_ARG, "storage_precision must be 32, 16 or 15 (BF16)");
+    if (P->storage_precision != 32 && P->storage_precision != 16 && P->storage_precision != HISQ_PREC_BF16 &&
+        P->storage_precision != HISQ_PREC_HALF_EV)
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "storage_precision must be 32, 16, 15 (BF16) or 14 (FP16 x 2^e)");
     if (!(P->tol > 0)) return set_err(ctx, HISQ_ERR_INVALID_ARG, "tol must be positive");
 
     // basis (n_kr + 1 vectors, Ritz vectors rotated into its head in place,
@@ -524,8 +536,9 @@ hisq_status hisq_set_eigvecs(hisq_ctx *ctx, int n, const double *vecs, const dou
 {
     if (!ctx) return HISQ_ERR_INVALID_ARG;
     if (n < 0 || (n > 0 && !vecs)) return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad eigenvector arguments");
-    if (storage_precision != 32 && storage_precision != 16 && storage_precision != HISQ_PREC_BF16)
-        return set_err(ctx, HISQ_ERR_INVALID_ARG, "storage_precision must be 32, 16 or 15 (BF16)");
+    if (storage_precision != 32 && storage_precision != 16 && storage_precision != HISQ_PREC_BF16 &&
+        storage_precision != HISQ_PREC_HALF_EV)
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "storage_precision must be 32, 16, 15 (BF16) or 14 (FP16 x 2^e)");
     if (!eps && !ctx->links_loaded) return set_err(ctx, HISQ_ERR_STATE, "links needed to recompute eigenvalues");
     HISQ_CUDA(cudaSetDevice(ctx->device));
     const int Vh = ctx->g.Vh;
@@ -610,7 +623,7 @@ hisq_status hisq_load_eigvecs(hisq_ctx *ctx, const char *path)
     bool ok = fread(&h, sizeof h, 1, fp) == 1 && memcmp(h.magic, "HISQEIG1", 8) == 0;
     const int Vh = ctx->g.Vh;
     ok = ok && h.dims[0] == ctx->g.X && h.dims[1] == ctx->g.Y && h.dims[2] == ctx->g.Z && h.dims[3] == ctx->g.T &&
-         (h.prec == 32 || h.prec == 16 || h.prec == HISQ_PREC_BF16) && h.n > 0 && h.bytes_per_vec == int64_t(spinor_bytes(h.prec, Vh));
+         (h.prec == 32 || h.prec == 16 || h.prec == HISQ_PREC_BF16 || h.prec == HISQ_PREC_HALF_EV) && h.n > 0 && h.bytes_per_vec == int64_t(spinor_bytes(h.prec, Vh));
     if (!ok) {
         fclose(fp);
         return set_err(ctx, HISQ_ERR_INVALID_ARG, "%s: bad header or lattice mismatch", path);

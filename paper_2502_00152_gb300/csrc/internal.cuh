@@ -189,11 +189,14 @@ __device__ __forceinline__ float stag_phase(int mu, const int c[4])
 //  FP32: [Vh] float4 (colours 0,1) then [Vh] float2 (colour 2)   24 B / site
 //  FP16: [Vh] uint4 = 6 halves (re,im x 3) + FP32 scale          16 B / site
 //  BF16: [3][Vh] bf16x2 (re,im), eigenvector storage only         12 B / site
+//  FP16 x 2^e: [3][Vh] half2 (re,im), eigenvector storage only     12 B / site
 //  DF64: [3][Vh] float4 (re hi, re lo, im hi, im lo), residuals only 48 B / site
 inline size_t spinor_bytes(int prec, int Vh)
 {
     return (prec == 64 || prec == HISQ_PREC_DF64) ? size_t(Vh) * 48
-                      : (prec == 32 ? size_t(Vh) * 24 : (prec == HISQ_PREC_BF16 ? size_t(Vh) * 12 : size_t(Vh) * 16));
+                      : (prec == 32 ? size_t(Vh) * 24
+                                    : ((prec == HISQ_PREC_BF16 || prec == HISQ_PREC_HALF_EV) ? size_t(Vh) * 12
+                                                                                            : size_t(Vh) * 16));
 }
 
 struct SpinorD {
@@ -311,6 +314,62 @@ struct SpinorB {
 };
 inline SpinorB make_spinorB(void *p, int Vh) { return SpinorB{(__nv_bfloat162 *)p, Vh}; }
 
+// FP16 eigenvector storage (HISQ_PREC_HALF_EV): FP16 values of v * 2^e,
+// colour-major like BF16 (12 B per site), with one power-of-two scale 2^e for
+// every site and vector, the smallest with 4^e >= 3 Vh.  A unit vector's
+// entries (|v| <= 1) then stay below 2 sqrt(3 Vh), inside the FP16 range for
+// every Vh below 3.5e8, and are O(1) on average; the scaling is exact, so the
+// stored value is the FP16 rounding of the FP32 value times 2^e.  The layout is
+// the tensor-core deflation operand as it is.
+__host__ __device__ __forceinline__ int ev_half_exponent(int Vh)
+{
+    const unsigned N = 3u * unsigned(Vh); // >= 3
+#ifdef __CUDA_ARCH__
+    const int lg = 32 - __clz(int(N - 1u)); // ceil(log2 N)
+#else
+    const int lg = 32 - __builtin_clz(N - 1u);
+#endif
+    return (lg + 1) / 2;
+}
+__host__ __device__ __forceinline__ float pow2f(int e)
+{
+    // 2^e for -126 <= e <= 127, exact
+    union {
+        unsigned u;
+        float f;
+    } b;
+    b.u = unsigned(127 + e) << 23;
+    return b.f;
+}
+
+struct SpinorE {
+    __half2 *p;
+    int Vh;
+    float s, inv; // 2^e and 2^-e
+    typedef float real;
+    __device__ __forceinline__ CVec<float> load(int i) const
+    {
+        CVec<float> v;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            const float2 f = __half22float2(p[size_t(c) * Vh + i]);
+            v.re[c] = f.x * inv;
+            v.im[c] = f.y * inv;
+        }
+        return v;
+    }
+    __device__ __forceinline__ void store(int i, const CVec<float> &v) const
+    {
+#pragma unroll
+        for (int c = 0; c < 3; c++) p[size_t(c) * Vh + i] = __floats2half2_rn(v.re[c] * s, v.im[c] * s);
+    }
+};
+__host__ __device__ inline SpinorE make_spinorE(void *p, int Vh)
+{
+    const int e = ev_half_exponent(Vh);
+    return SpinorE{(__half2 *)p, Vh, pow2f(e), pow2f(-e)};
+}
+
 // accessor of the same storage type as S for another field
 template <class S>
 inline S make_like(void *p, int Vh);
@@ -322,6 +381,8 @@ template <>
 inline SpinorH make_like<SpinorH>(void *p, int Vh) { return make_spinorH(p, Vh); }
 template <>
 inline SpinorB make_like<SpinorB>(void *p, int Vh) { return make_spinorB(p, Vh); }
+template <>
+inline SpinorE make_like<SpinorE>(void *p, int Vh) { return make_spinorE(p, Vh); }
 
 // convert between accumulation types
 template <typename To, typename From>
@@ -631,7 +692,6 @@ enum BufId : int {
     BUF_TEST_A,
     BUF_TEST_B,
     BUF_TEST_C,
-    BUF_EPS,           // eigenvalues on the device (FP64)
     BUF_EIG_Y,         // Ritz rotation matrix (FP64)
     BUF_EIG_W,         // eigensolver work vectors
     BUF_B_Y,           // batched solve: k FP64 right-hand sides y_e
@@ -656,9 +716,10 @@ enum BufId : int {
 
 struct EigenStore {
     int n = 0;            // stored eigenpairs
-    int prec = 32;        // storage precision (32, 16 or HISQ_PREC_BF16)
+    int prec = 32;        // storage precision (32, 16, HISQ_PREC_BF16 or HISQ_PREC_HALF_EV)
     void *vecs = nullptr; // n vectors of spinor_bytes(prec, Vh)
     std::vector<double> eps; // massless eigenvalues, ascending
+    double *eps_dev = nullptr; // device copy of eps, written when the pairs are stored
     unsigned version = 0;    // bumped whenever the stored pairs change
 };
 

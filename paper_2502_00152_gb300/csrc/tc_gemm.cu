@@ -13,10 +13,11 @@
 // residual part and three MMAs (hi*hi + hi*lo + lo*hi) are accumulated, which
 // gives about 22 significant bits: enough for the updated residual to stay
 // consistent with the updated solution (r -= V c uses A v_i = lambda_i v_i).
-// BF16 eigenvectors: the stored vectors are the A operand as they are (their
-// colour-major layout is the GEMM's K order); only the other operand is split
-// into BF16 high and low parts, two MMAs (a*hi + a*lo) per step, so the
-// products are those of the stored vectors to about 16 bits of the other side.
+// BF16 or FP16 (HISQ_PREC_HALF_EV) eigenvectors: the stored vectors are the A
+// operand as they are (their colour-major layout is the GEMM's K order); only
+// the other operand is split into high and low parts of the same type, two MMAs
+// (a*hi + a*lo) per step, so the products are those of the stored vectors to
+// about 16 (BF16) or 22 (FP16) bits of the other side.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -24,6 +25,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -101,7 +103,12 @@ struct ExpandEpi {
 // only access TMEM lanes 32 * (w % 4) .. +31, so these four cover all 128 rows).
 constexpr int TC_THREADS = 192;
 
-template <int MT, int N, int STAGES, int MODE, bool BF16>
+// operand kinds of A (the eigenvectors): FP16 high + low parts of FP32 vectors,
+// stored BF16 vectors, stored FP16 vectors; B is split into high and low parts
+// of A's type in every case
+enum : int { AK_F16_SPLIT = 0, AK_BF16 = 1, AK_F16 = 2 };
+
+template <int MT, int N, int STAGES, int MODE, int AK>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
               const __grid_constant__ CUtensorMap tmBh, const __grid_constant__ CUtensorMap tmBl, int K, int kchunk,
@@ -109,10 +116,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 {
     constexpr int A_TILE = 128 * TC_ROWB;               // 16 KB per 128-row tile
     constexpr int B_TILE = N * TC_ROWB;
-    constexpr int AP = BF16 ? 1 : 2;                      // A parts: hi (+ lo for FP16)
+    constexpr int AP = AK == AK_F16_SPLIT ? 2 : 1;        // A parts: hi (+ lo for split FP32)
     constexpr int STAGE = AP * MT * A_TILE + 2 * B_TILE;  // B: hi + lo
     constexpr int NCOLS = (MT * N <= 32) ? 32 : (MT * N <= 64) ? 64 : (MT * N <= 128) ? 128 : (MT * N <= 256) ? 256 : 512;
-    constexpr uint32_t IDESC = BF16 ? tc::idesc_bf16_f32(128, N) : tc::idesc_f16_f32(128, N);
+    constexpr uint32_t IDESC = AK == AK_BF16 ? tc::idesc_bf16_f32(128, N) : tc::idesc_f16_f32(128, N);
     static_assert(N % 16 == 0 && N >= 16 && N <= 256, "N");
     static_assert(MT * N <= 512, "TMEM columns");
 
@@ -159,7 +166,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer
         tc::prefetch_tmap(&tmAh);
-        if (!BF16) tc::prefetch_tmap(&tmAl);
+        if (AK == AK_F16_SPLIT) tc::prefetch_tmap(&tmAl);
         tc::prefetch_tmap(&tmBh);
         tc::prefetch_tmap(&tmBl);
         uint32_t it = 0;
@@ -174,7 +181,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int kx = kbeg + kk * TC_BK;
                 for (int mt = 0; mt < MT; mt++) {
                     tc::tma_load_2d(st + mt * A_TILE, &tmAh, &full[s], kx, m0 + mt * 128);
-                    if (!BF16) tc::tma_load_2d(st + (MT + mt) * A_TILE, &tmAl, &full[s], kx, m0 + mt * 128);
+                    if (AK == AK_F16_SPLIT) tc::tma_load_2d(st + (MT + mt) * A_TILE, &tmAl, &full[s], kx, m0 + mt * 128);
                 }
                 tc::tma_load_2d(st + AP * MT * A_TILE, &tmBh, &full[s], kx, 0);
                 tc::tma_load_2d(st + AP * MT * A_TILE + B_TILE, &tmBl, &full[s], kx, 0);
@@ -209,7 +216,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const uint32_t acc0 = (kk > 0 || q > 0) ? 1u : 0u;
                         tc::mma_f16(d, tc::smem_desc_sw128(ah + off), tc::smem_desc_sw128(bh + off), IDESC, acc0);
                         tc::mma_f16(d, tc::smem_desc_sw128(ah + off), tc::smem_desc_sw128(bl + off), IDESC, 1u);
-                        if (!BF16)
+                        if (AK == AK_F16_SPLIT)
                             tc::mma_f16(d, tc::smem_desc_sw128(al + off), tc::smem_desc_sw128(bh + off), IDESC, 1u);
                     }
                 }
@@ -407,7 +414,7 @@ __global__ void k_reduce_part(int nsplit, int n, int Mrows, int N, int ncol, con
 struct TcState {
     unsigned version = ~0u;     // eigenpair version the copies were built from
     int n = 0, Vh = 0;
-    bool bf16 = false;          // BF16 storage: vm_hi is the stored vectors, no lo parts
+    int akind = AK_F16_SPLIT;   // AK_BF16 / AK_F16: vm_hi is the stored vectors, no lo parts
     void *vm_hi = nullptr, *vm_lo = nullptr, *sm_hi = nullptr, *sm_lo = nullptr;
     void *owned = nullptr;      // device copies owned by this state
     size_t ld_sm = 0;           // 16-bit values per site-major row
@@ -445,18 +452,19 @@ static hisq_status tc_prepare_v(hisq_ctx *ctx, int n)
     TcState &S = tc_state(ctx);
     const int Vh = ctx->g.Vh;
     if (S.version == ctx->eig.version && S.n == n && S.Vh == Vh && S.vm_hi) return HISQ_OK;
-    if (ctx->eig.prec != 32 && ctx->eig.prec != HISQ_PREC_BF16)
-        return set_err(ctx, HISQ_ERR_INVALID_ARG, "tensor-core deflation needs FP32 or BF16 eigenvectors");
+    if (ctx->eig.prec != 32 && ctx->eig.prec != HISQ_PREC_BF16 && ctx->eig.prec != HISQ_PREC_HALF_EV)
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "tensor-core deflation needs FP32, BF16 or FP16 (14) eigenvectors");
     tc_release(ctx);
     const size_t L = size_t(3) * Vh;
     const size_t ld_sm = ((size_t(2) * n + 63) / 64) * 64; // 16-bit values per site-major row (128 B multiple)
-    if (ctx->eig.prec == HISQ_PREC_BF16) {
+    if (ctx->eig.prec == HISQ_PREC_BF16 || ctx->eig.prec == HISQ_PREC_HALF_EV) {
         // the stored vectors are the projection operand; build the site-major copy
+        // (a transpose of 32-bit (re, im) pairs, the same for both 16-bit types)
         const size_t bytes = L * ld_sm * sizeof(__nv_bfloat16);
         void *sm = dev_alloc(ctx, bytes);
         if (!sm) return HISQ_ERR_OOM;
         HISQ_CUDA(cudaMemsetAsync(sm, 0, bytes, ctx->stream));
-        S.bf16 = true;
+        S.akind = ctx->eig.prec == HISQ_PREC_BF16 ? AK_BF16 : AK_F16;
         S.vm_hi = ctx->eig.vecs;
         S.sm_hi = sm;
         S.owned = sm;
@@ -465,7 +473,8 @@ static hisq_status tc_prepare_v(hisq_ctx *ctx, int n)
         S.n = n;
         S.Vh = Vh;
         S.version = ctx->eig.version;
-        S.sigma = 1.f;
+        // FP16 vectors are stored times 2^e (exact); BF16 ones unscaled
+        S.sigma = S.akind == AK_F16 ? pow2f(ev_half_exponent(Vh)) : 1.f;
         ctx->launches++;
         dim3 grid(unsigned((L + 31) / 32), unsigned((n + 31) / 32));
         k_build_v_sm_bf16<<<grid, dim3(32, 8), 0, ctx->stream>>>(int(L), n, (const __nv_bfloat162 *)ctx->eig.vecs, L,
@@ -497,14 +506,14 @@ static hisq_status tc_prepare_v(hisq_ctx *ctx, int n)
     return HISQ_OK;
 }
 
-template <int MT, int N, int ST, int MODE, bool BF16>
+template <int MT, int N, int ST, int MODE, int AK>
 static hisq_status launch_gemm(hisq_ctx *ctx, dim3 grid, const CUtensorMap *m, int K, int kchunk, int Mrows, float *part,
                                ExpandEpi epi, int *status)
 {
-    constexpr int STAGE = (BF16 ? 1 : 2) * MT * 128 * TC_ROWB + 2 * N * TC_ROWB;
+    constexpr int STAGE = (AK == AK_F16_SPLIT ? 2 : 1) * MT * 128 * TC_ROWB + 2 * N * TC_ROWB;
     const size_t smem = size_t(ST) * STAGE + 1024 + 256;
     static_assert(ST * STAGE + 1024 + 256 <= 227 * 1024, "shared memory");
-    auto kern = k_tc_gemm<MT, N, ST, MODE, BF16>;
+    auto kern = k_tc_gemm<MT, N, ST, MODE, AK>;
     static bool attr = false;
     if (!attr) {
         HISQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
@@ -568,7 +577,8 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
     const int NP = 64;                        // 2k <= 64 columns, padded by zero fill
     std::vector<float> sc(k);
     for (int j = 0; j < k; j++) sc[j] = rnorm[j] > 0 ? float(std::sqrt(double(L)) / rnorm[j]) : 1.f;
-    const bool bf = S.bf16;
+    const int ak = S.akind;
+    const bool bf = ak == AK_BF16, single = ak != AK_F16_SPLIT;
     const size_t rbytes = size_t(2) * k * L * 2 * sizeof(__half); // same size for BF16
     char *w = (char *)get_buf(ctx, BUF_TC_WORK, 2 * rbytes + 4096 + sizeof(float) * 8 * 64);
     if (!w) return HISQ_ERR_OOM;
@@ -592,14 +602,14 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
 
     CUtensorMap mp[4];
     const uint64_t Kp = uint64_t(2) * L;
-    const void *alo = bf ? S.vm_hi : S.vm_lo; // BF16: no low part (the map is not read)
+    const void *alo = single ? S.vm_hi : S.vm_lo; // stored 16-bit vectors: no low part (the map is not read)
     if (!make_tmap(&mp[0], S.vm_hi, Kp, n, Kp * 2, 128, bf) || !make_tmap(&mp[1], alo, Kp, n, Kp * 2, 128, bf) ||
         !make_tmap(&mp[2], rh, Kp, 2 * k, Kp * 2, NP, bf) || !make_tmap(&mp[3], rl, Kp, 2 * k, Kp * 2, NP, bf))
         return set_err(ctx, HISQ_ERR_CUDA, "tensor map encoding failed");
     // split K over about one CTA per SM; rows per CTA: FP16 hi + lo A tiles of
     // 256 rows, or BF16 A tiles of 512 rows, with B fit two 80 KB stages
     const int mtiles = (n + 127) / 128;
-    const int MTP = bf ? (mtiles >= 4 ? 4 : (mtiles >= 2 ? 2 : 1)) : 2;
+    const int MTP = single ? (mtiles >= 4 ? 4 : (mtiles >= 2 ? 2 : 1)) : 2;
     const int mgroups = (mtiles + MTP - 1) / MTP;
     int nsplit = std::max(1, ctx->num_sms / mgroups);
     int kchunk = int(((Kp + nsplit - 1) / nsplit + TC_BK - 1) / TC_BK) * TC_BK;
@@ -609,18 +619,19 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
     double *C = (double *)get_buf(ctx, BUF_TC_C, sizeof(double) * size_t(n) * 2 * k);
     if (!part || !C) return HISQ_ERR_OOM;
     ExpandEpi none{};
-    if (bf && MTP == 4)
-        TRY_HISQ((launch_gemm<4, NP, 2, 0, true>(ctx, dim3(nsplit, mgroups), mp, int(Kp), kchunk, Mrows, part, none,
-                                                status)));
-    else if (bf && MTP == 2)
-        TRY_HISQ((launch_gemm<2, NP, 2, 0, true>(ctx, dim3(nsplit, mgroups), mp, int(Kp), kchunk, Mrows, part, none,
-                                                status)));
-    else if (bf)
-        TRY_HISQ((launch_gemm<1, NP, 4, 0, true>(ctx, dim3(nsplit, mgroups), mp, int(Kp), kchunk, Mrows, part, none,
-                                                status)));
+    const dim3 pgrid(nsplit, mgroups);
+    auto project = [&](auto akc) -> hisq_status {
+        constexpr int AKC = decltype(akc)::value;
+        if (MTP == 4) return launch_gemm<4, NP, 2, 0, AKC>(ctx, pgrid, mp, int(Kp), kchunk, Mrows, part, none, status);
+        if (MTP == 2) return launch_gemm<2, NP, 2, 0, AKC>(ctx, pgrid, mp, int(Kp), kchunk, Mrows, part, none, status);
+        return launch_gemm<1, NP, 4, 0, AKC>(ctx, pgrid, mp, int(Kp), kchunk, Mrows, part, none, status);
+    };
+    if (ak == AK_BF16)
+        TRY_HISQ(project(std::integral_constant<int, AK_BF16>{}));
+    else if (ak == AK_F16)
+        TRY_HISQ(project(std::integral_constant<int, AK_F16>{}));
     else
-        TRY_HISQ((launch_gemm<2, NP, 2, 0, false>(ctx, dim3(nsplit, mgroups), mp, int(Kp), kchunk, Mrows, part, none,
-                                                 status)));
+        TRY_HISQ((launch_gemm<2, NP, 2, 0, AK_F16_SPLIT>(ctx, pgrid, mp, int(Kp), kchunk, Mrows, part, none, status)));
     ctx->launches++;
     k_reduce_part<<<(n * 2 * k + 255) / 256, 256, 0, ctx->stream>>>(nsplit, n, Mrows, NP, 2 * k, part, C);
     HISQ_CUDA(cudaGetLastError());
@@ -687,7 +698,7 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
     // the TMA box of D' is as tall as the kernel's N (rows beyond NEP are zero filled)
     const int NT = NEP <= 32 ? 32 : (NEP <= 64 ? 64 : 128);
     CUtensorMap me[4];
-    const void *slo = bf ? S.sm_hi : S.sm_lo;
+    const void *slo = single ? S.sm_hi : S.sm_lo;
     if (!make_tmap(&me[0], S.sm_hi, ldk, L, S.ld_sm * 2, 128, bf) || !make_tmap(&me[1], slo, ldk, L, S.ld_sm * 2, 128, bf) ||
         !make_tmap(&me[2], ddh, ldk, NEP, size_t(ldk) * 2, NT, bf) ||
         !make_tmap(&me[3], ddl, ldk, NEP, size_t(ldk) * 2, NT, bf))
@@ -696,15 +707,16 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
     const int ntiles = (L + 127) / 128;
     const int grid = std::min(ntiles, ctx->num_sms);
     hisq_status st;
-    if (bf) {
-        if (NT == 32) st = launch_gemm<1, 32, 4, 1, true>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
-        else if (NT == 64) st = launch_gemm<1, 64, 4, 1, true>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
-        else st = launch_gemm<1, 128, 4, 1, true>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
-    } else {
-        if (NT == 32) st = launch_gemm<1, 32, 4, 1, false>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
-        else if (NT == 64) st = launch_gemm<1, 64, 4, 1, false>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
-        else st = launch_gemm<1, 128, 3, 1, false>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
-    }
+    auto expand = [&](auto akc) -> hisq_status {
+        constexpr int AKC = decltype(akc)::value;
+        if (NT == 32) return launch_gemm<1, 32, 4, 1, AKC>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
+        if (NT == 64) return launch_gemm<1, 64, 4, 1, AKC>(ctx, dim3(grid), me, ldk, ldk, L, nullptr, epi, status);
+        return launch_gemm<1, 128, (AKC == AK_F16_SPLIT ? 3 : 4), 1, AKC>(ctx, dim3(grid), me, ldk, ldk, L, nullptr,
+                                                                          epi, status);
+    };
+    if (ak == AK_BF16) st = expand(std::integral_constant<int, AK_BF16>{});
+    else if (ak == AK_F16) st = expand(std::integral_constant<int, AK_F16>{});
+    else st = expand(std::integral_constant<int, AK_F16_SPLIT>{});
     if (st != HISQ_OK) return st;
     HISQ_CUDA(cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     HISQ_CUDA(cudaStreamSynchronize(ctx->stream));

@@ -35,6 +35,7 @@ HISQ_PREC_DOUBLE = 64
 HISQ_PREC_SINGLE = 32
 HISQ_PREC_HALF = 16
 HISQ_PREC_BF16 = 15  # eigenvector storage only
+HISQ_PREC_HALF_EV = 14  # FP16 of v * 2^e (4^e >= 3 Vh), 12 B per site; eigenvector storage only
 HISQ_PREC_DF64 = 48  # double-float (FP32 hi + lo) reliable-update residuals and test operators
 
 

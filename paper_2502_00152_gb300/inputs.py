@@ -116,19 +116,33 @@ def _reunitarise(u: np.ndarray) -> np.ndarray:
     return np.stack([r0, r1, r2], axis=1)
 
 
+def _workers() -> int:
+    import os
+
+    return max(1, min(16, os.cpu_count() or 1))
+
+
 def thin_links(dims, seed: int, eps: float, chunk: int = 1 << 20) -> np.ndarray:
-    """Thin SU(3) links U_mu(x) = exp(i eps A), layout [s][mu][3][3]."""
+    """Thin SU(3) links U_mu(x) = exp(i eps A), layout [s][mu][3][3].  Chunks of
+    links are independent (counter-based deviates), so they are computed on a
+    pool of threads; the result does not depend on the number of threads."""
+    from concurrent.futures import ThreadPoolExecutor
+
     import torch
 
     check_dims(dims)
     n = volume(dims) * 4
     out = np.empty((n, 3, 3), dtype=np.complex128)
-    for c0 in range(0, n, chunk):
+
+    def one(c0):
         c1 = min(n, c0 + chunk)
         om = random_normal(seed, STREAM_LINK, 8 * c0, 8 * (c1 - c0)).reshape(c1 - c0, 8)
         a = np.einsum("na,aij->nij", om, _LAMBDA) * 0.5
         u = torch.linalg.matrix_exp(torch.from_numpy(1j * eps * a)).numpy()
         out[c0:c1] = _reunitarise(u)
+
+    with ThreadPoolExecutor(max_workers=_workers()) as ex:
+        list(ex.map(one, range(0, n, chunk)))
     return out.reshape(volume(dims), 4, 3, 3)
 
 
@@ -141,15 +155,25 @@ def _shift_forward(field: np.ndarray, dims, mu: int, n: int) -> np.ndarray:
 
 
 def hisq_links(dims, seed: int, eps: float, c1: float = C1_NAIK, c3: float = C3_NAIK):
-    """Fat and long links of the synthetic recipe: (fat, long), each [s][mu][3][3]."""
+    """Fat and long links of the synthetic recipe: (fat, long), each [s][mu][3][3].
+    The products of three thin links are batched 3x3 complex matrix products
+    (torch.bmm on the host, in chunks)."""
+    import torch
+
     u = thin_links(dims, seed, eps)
     fat = c1 * u
     lng = np.empty_like(u)
+    chunk = 1 << 20
     for mu in range(4):
-        umu = u[:, mu]
+        umu = np.ascontiguousarray(u[:, mu])
         u1 = _shift_forward(umu, dims, mu, 1)
         u2 = _shift_forward(umu, dims, mu, 2)
-        lng[:, mu] = c3 * (umu @ u1 @ u2)
+        for s0 in range(0, len(umu), chunk):
+            s1 = min(len(umu), s0 + chunk)
+            p = torch.bmm(torch.bmm(torch.from_numpy(umu[s0:s1]), torch.from_numpy(u1[s0:s1])),
+                          torch.from_numpy(u2[s0:s1]))
+            lng[s0:s1, mu] = c3 * p.numpy()
+        del umu, u1, u2
     return fat, lng
 
 

@@ -76,7 +76,12 @@ def test_batched_deflated_with_redeflation():
 
 def test_batched_full_size_z2_walls():
     """24 Z2 wall sources (8 timeslices x 3 colours) on the 32^3x64 lattice,
-    one batched solve; every solution meets 1e-10 under the oracle operator."""
+    one batched solve, plain and deflated (64 eigenpairs from the library's
+    block thick-restart Lanczos, BF16 storage as in the batched benchmark, so the
+    tensor-core deflation with its re-deflations runs at full size); every
+    solution meets 1e-10 under the oracle operator, and deflation removes
+    iterations from every right-hand side (a wrong deflation would still
+    converge, but only with more iterations)."""
     c = I.lattice_config("c3")
     dims, m = c["dims"], c["mass"]
     ctx, o = make(dims, seed=c["seed"], eps=c["eps"], mass=m)
@@ -86,5 +91,17 @@ def test_batched_full_size_z2_walls():
         assert status == H.HISQ_OK
         for j in (0, 7, 13, 23):
             assert o.full_residual(m, psi[j], etas[j]) <= 1e-10
+        plain_it = [s["iterations"] for s in st]
+        eps, nconv = H.hisq_eigensolve(ctx, H.hisq_default_eig_params(
+            n_ev=64, n_kr=192, tol=1e-6, max_restarts=100, cheby_degree=60, a_min=-2.0,
+            storage_precision=H.HISQ_PREC_BF16, seed=5, block_size=32))
+        assert nconv == 64
+        psi, st, status = H.hisq_solve(ctx, etas, H.hisq_default_solve_params(batch=1, deflate=1,
+                                                                             precision_sloppy=16))
+        assert status == H.HISQ_OK
+        for j in (0, 5, 11, 16, 23):
+            assert o.full_residual(m, psi[j], etas[j]) <= 1e-10
+        for j in range(24):
+            assert st[j]["iterations"] <= 0.9 * plain_it[j], (j, st[j]["iterations"], plain_it[j])
     finally:
         ctx.close()

@@ -1,0 +1,138 @@
+"""Parity at the sizes where the production code paths run.
+
+Small lattices leave some paths of the deflation and the eigensolver idle:
+  * the CUDA-core projection of Eq. 4 sums per-chunk partials of 4096 sites,
+    so it needs Vh > 4096 (several chunks, a ragged last one) to test the
+    cross-chunk reduction;
+  * the tensor-core projection splits K over about one CTA per SM and reuses
+    its shared-memory ring only when a CTA gets more k-tiles than stages; the
+    expansion reuses its tensor-memory accumulator (the `drained` wait) only
+    when a CTA gets two or more row tiles;
+  * thick-restart Lanczos runs its stochastic window estimate, the Chebyshev
+    filter and the block-size reduction only at the benchmark's settings.
+Eq. 4 is a plain formula, so for these sizes the eigenvectors are host-QR
+orthonormal sets of seeded Gaussian even-site fields with chosen eigenvalues,
+for which the oracle's deflated guess is exact.  The eigensolver at 24^3 x 48 is
+pinned by the oracle's FP64 Rayleigh quotients and residuals of each returned
+vector, orthonormality, and agreement with a run from another start vector
+within the Kato-Temple bound."""
+import numpy as np
+import pytest
+
+from gpu_common import make, orthonormal_even_set, rel, stored_vectors
+from oracle.oracle import deflation_guess, even_sites, project_parity, site_parity
+from paper_2502_00152_gb300 import hisq as H
+from paper_2502_00152_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("storage", [32, 16, H.HISQ_PREC_BF16, H.HISQ_PREC_HALF_EV])
+def test_deflation_many_chunks_matches_oracle(storage):
+    """16^3 x 32: Vh = 65,536 = 16 projection chunks per vector."""
+    dims = (16, 16, 16, 32)
+    m = 0.002
+    n = 64
+    ctx, _ = make(dims, seed=2, eps=0.3, mass=m)
+    try:
+        lam, vecs = orthonormal_even_set(dims, n, seed=11)
+        H.hisq_set_eigvecs(ctx, vecs, lam, storage)
+        vs = stored_vectors(vecs, storage, I.volume(dims) // 2)
+        for seed in (41, 42):
+            b = project_parity(dims, I.gaussian_field(dims, seed), 0)
+            x = H.hisq_deflate(ctx, b)
+            ref = deflation_guess(vs, lam + 4 * m * m, b)
+            assert rel(x, ref) <= 2e-6, (storage, rel(x, ref))
+            assert np.all(x[site_parity(dims) == 1] == 0)
+    finally:
+        ctx.close()
+
+
+# (storage, n, k): the benchmark shapes of the batched deflation (512 BF16
+# vectors and 24 right-hand sides; 200 FP16 vectors and 12 right-hand sides)
+# and the other template variants (FP32 high/low split; one A tile per CTA)
+@pytest.mark.parametrize("storage,n,k", [(H.HISQ_PREC_BF16, 512, 24), (H.HISQ_PREC_HALF_EV, 200, 12),
+                                         (H.HISQ_PREC_HALF_EV, 64, 24), (32, 130, 12)])
+def test_tc_deflation_ring_and_tmem_reuse(storage, n, k):
+    """12^3 x 16: L = 3 Vh = 41,472 rows.  The projection gives each of ~152
+    CTAs >= 9 k-tiles of 64 (more than its 2 or 4 stages), the expansion 2-3
+    row tiles of 128 per CTA."""
+    dims = (12, 12, 12, 16)
+    m = 0.002
+    ctx, _ = make(dims, seed=2, eps=0.3, mass=m)
+    try:
+        lam, vecs = orthonormal_even_set(dims, n, seed=12)
+        H.hisq_set_eigvecs(ctx, vecs, lam, storage)
+        vs = stored_vectors(vecs, storage, I.volume(dims) // 2)
+        ev = even_sites(dims)
+        Vm = vs[:, ev, :].reshape(n, -1)
+        bs = np.stack([project_parity(dims, I.gaussian_field(dims, 60 + j), 0) for j in range(k)])
+        x, r = H.hisq_deflate_batch(ctx, bs)
+        # FP32 split (~22 bits), FP16 stored x FP16 high/low (~22 bits),
+        # BF16 stored x BF16 high/low (~16 bits of the residual side)
+        tol = 1e-4 if storage == H.HISQ_PREC_BF16 else 1e-5
+        for j in range(k):
+            ref = deflation_guess(vs, lam + 4 * m * m, bs[j])
+            assert rel(x[j], ref) <= tol, (j, rel(x[j], ref))
+            be = bs[j][ev].reshape(-1)
+            rref = np.zeros_like(bs[j])
+            rref[ev] = (be - Vm.T @ (Vm.conj() @ be)).reshape(-1, 3)
+            assert rel(r[j], rref) <= tol, (j, rel(r[j], rref))
+    finally:
+        ctx.close()
+
+
+def _kato_temple_ok(e1, r1, e2, r2):
+    """|e1_i - e2_i| within res_1^2/gap + res_2^2/gap (+ rounding) for every pair
+    whose gap to its neighbours (from run 1) is resolved; the last pair, whose
+    upper neighbour was not computed, is skipped."""
+    n = len(e1)
+    bad = []
+    for i in range(n - 1):
+        gap = e1[i + 1] - e1[i] if i == 0 else min(e1[i + 1] - e1[i], e1[i] - e1[i - 1])
+        if gap <= 1e-6 * e1[i]:
+            continue  # (near-)degenerate: only the cluster is defined
+        bound = (r1[i] ** 2 + r2[i] ** 2) / gap + 1e-12 * e1[i]
+        if abs(e1[i] - e2[i]) > bound:
+            bad.append((i, e1[i], e2[i], bound))
+    return bad
+
+
+def test_trlm_benchmark_settings_24c48():
+    """Thick-restart Lanczos at 24^3 x 48 (the learned-guess lattice, seed 3,
+    eps 0.3) with the benchmark's settings: stochastic window (a_min = -2),
+    Chebyshev degree 60, block 32 (and 16 for the second run), n_kr = 3 n_ev."""
+    c = I.lattice_config("c4")
+    dims = c["dims"]
+    ctx, o = make(dims, seed=c["seed"], eps=c["eps"], mass=c["mass"])
+    n_ev = 64
+    try:
+        runs = []
+        for seed, block in ((101, 32), (202, 16)):
+            prm = H.hisq_default_eig_params(n_ev=n_ev, n_kr=3 * n_ev, tol=1e-6, max_restarts=100, cheby_degree=60,
+                                            a_min=-2.0, a_max=0.0, storage_precision=32, seed=seed,
+                                            block_size=block)
+            eps, nconv = H.hisq_eigensolve(ctx, prm)
+            assert nconv == n_ev
+            assert np.all(np.diff(eps) >= 0)
+            ev = even_sites(dims)
+            res = np.zeros(n_ev)
+            G = np.zeros((n_ev, 3 * len(ev)), dtype=np.complex128)
+            for i in range(n_ev):
+                v = H.hisq_get_eigvec(ctx, i)
+                assert np.all(project_parity(dims, v, 1) == 0)
+                th, res[i] = o.rayleigh(0.0, v)
+                # the library's eigenvalue is the FP64 Rayleigh quotient of the
+                # stored vector: the oracle's operator gives the same number
+                assert abs(th - eps[i]) <= 1e-8 * eps[i], (i, th, eps[i])
+                G[i] = v[ev].reshape(-1)
+            # residual |A v - theta v| within the tolerance (1e-6 x a_max, a_max
+            # about 1.1 x 22) plus the FP32 rounding of the stored vector
+            assert np.max(res) <= 3e-5, np.max(res)
+            gram = G.conj() @ G.T
+            assert np.max(np.abs(gram - np.eye(n_ev))) <= 1e-5
+            runs.append((eps, res))
+        (e1, r1), (e2, r2) = runs
+        assert _kato_temple_ok(e1, r1, e2, r2) == []
+    finally:
+        ctx.close()
