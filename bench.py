@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--plain-warmup", type=int, default=None,
                     help="warm-up steps of the plain-CG comparison (default: --warmup)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end host-API measurement")
+    ap.add_argument("--source-pool-gb", type=float, default=30.0,
+                    help="device memory for distinct source batches (cycled over the steps)")
     ap.add_argument("--cpu-iters", type=int, default=2, help="oracle CG iterations per CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--learned", action="store_true", help="learned initial guess workload (24^3x48)")
@@ -86,6 +88,8 @@ def parse():
     ap.add_argument("--tc", type=int, default=0, help="--capture: also run the tensor-core batched deflation "
                                                       "with this many random eigenvectors (24 RHS)")
     ap.add_argument("--tc-prec", type=int, default=32, help="--capture: eigenvector storage for --tc (32, 15, 14)")
+    ap.add_argument("--mrhs-shape", default=None, metavar="KIND,R,BUDGET",
+                    help="--capture: fixed launch shape of the batched operator (hisq_set_batched_kernel)")
     ap.add_argument("--traffic-from", default=None, metavar="REPORT",
                     help="--capture: write profiles/dslash_traffic.json from an ncu report of a capture run")
     ap.add_argument("--traffic-key", default="s16_r12", help="--capture: key suffix (sloppy bits, recon)")
@@ -259,7 +263,10 @@ def run_ours(a):
     kps = a.rhs_per_step if a.rhs_per_step is not None else {"c3": 24, "c5": 12}.get(a.config, 1)
     plain_steps = a.steps if a.plain_steps is None else a.plain_steps
     plain_warmup = a.warmup if a.plain_warmup is None else a.plain_warmup
-    nsrc = a.warmup + a.steps
+    # a pool of distinct source batches, resident in HBM, cycled over the steps
+    # (a 12-RHS batch of the largest lattice is 14.5 GB of FP64 fields)
+    batch_bytes = V * 48 * kps
+    nsrc = max(1, min(a.warmup + a.steps, int(a.source_pool_gb * 1e9 // batch_bytes)))
     if kps == 1:
         srcs = [I.gaussian_source(dims, SOURCE_SEED, rank * 1000 + k) for k in range(nsrc)]
     elif a.config == "c5":
@@ -331,7 +338,7 @@ def run_ours(a):
     plain, _, plain_ms, _, _ = timed(prm_plain, plain_warmup, plain_steps) if plain_steps > 0 else ([], 0, None, 0, None)
 
     # end to end through the host API: pinned host source -> psi on the host
-    pin_eta = torch.from_numpy(np.ascontiguousarray(srcs[a.warmup])).pin_memory()
+    pin_eta = torch.from_numpy(np.ascontiguousarray(srcs[a.warmup % nsrc])).pin_memory()
     e2e_ms = []
     for k in range(max(1, a.e2e_steps)):
         torch.cuda.synchronize()
@@ -345,16 +352,16 @@ def run_ours(a):
     # the double-float links need as much memory as the FP64 copy (2304 B per
     # site), which the largest workload does not have left
     other = 64 if rel_prec != 64 else H.HISQ_PREC_DF64
-    other_rel = None
-    if a.config == "c5" and other == H.HISQ_PREC_DF64:
-        other_rel = {"unavailable": "double-float links (2304 B per site, 58 GB) do not fit beside this workload"}
-    else:
-        try:
-            s2, e2, v2, _, _ = timed(params(1 if n_ev > 0 else 0, other), 1, 1)
-            other_rel = {"ms_per_rhs": round(v2, 3), "iterations": s2[0]["iterations"],
-                         "reliable_updates": s2[0]["reliable_updates"], "true_residual_max": s2[0]["full_residual"]}
-        except Exception as e:  # e.g. no room for the double-float links
-            other_rel = {"unavailable": str(e)[:200]}
+    mem = {"library_bytes_before_comparison": H.hisq_device_bytes(ctx),
+           "device_free_bytes_before_comparison": torch.cuda.mem_get_info(local)[0]}
+    try:
+        s2, e2, v2, _, _ = timed(params(1 if n_ev > 0 else 0, other), 1, max(1, min(2, a.steps)))
+        other_rel = {"ms_per_rhs": round(v2, 3), "iterations": [x["iterations"] for x in s2],
+                     "reliable_updates": [x["reliable_updates"] for x in s2],
+                     "true_residual_max": max(x["full_residual"] for x in s2)}
+    except Exception as e:  # e.g. no room for the double-float links
+        other_rel = {"unavailable": str(e)[:200]}
+    mem["library_bytes_after_comparison"] = H.hisq_device_bytes(ctx)
 
     # Dslash roofline from the event-timed kernels of the timed solves
     it = sum(s["profiled_iterations"] for s in stats)
@@ -434,6 +441,7 @@ def run_ours(a):
             "l2": "inputs larger than L2 (links and eigenvectors are GBs)",
             "parallelism": f"replicas{world}",
             "graphs": "on (CG iterations replayed as CUDA graphs on the library's stream)",
+            "sources": f"{nsrc} distinct batches resident in HBM, cycled over the steps",
         },
         "roofline": roof,
         "e2e": {"value": round(sorted(e2e_ms)[len(e2e_ms) // 2], 4), "unit": "ms/RHS",
@@ -455,6 +463,7 @@ def run_ours(a):
         "eigensolve_break_even_rhs": (round(eig["seconds"] * 1e3 / (plain_ms - value), 1)
                                       if eig and plain_ms and plain_ms > value else None),
         "link_generation_s": round(t_links, 2),
+        "device_memory": mem,
     }
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(a, dims, cfg, 1, *keep_links)
@@ -566,6 +575,8 @@ def run_capture(a):
     ctx = H.hisq_create(dims, t_antiperiodic=True, device=0)
     H.hisq_load_links(ctx, fat, lng, long_recon=a.recon, long_scale=I.C3_NAIK if a.recon != 18 else 1.0)
     H.hisq_set_mass(ctx, c["mass"])
+    if a.mrhs_shape:
+        H.hisq_set_batched_kernel(ctx, *[int(x) for x in a.mrhs_shape.split(",")])
     if a.mrhs > 1:
         import numpy as np
 

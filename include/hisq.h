@@ -195,6 +195,28 @@ hisq_status hisq_set_mass(hisq_ctx *ctx, double m);
 hisq_status hisq_apply_dslash(hisq_ctx *ctx, int out_parity, int precision, int link_precision,
                               const double *in, double *out);
 
+/* The batched operator of the multi-RHS solve (test entry point): for nrhs <= 64
+ * host full-lattice fields in_j (offset j*V*6 doubles), out_parity sites of
+ * out_j = D applied to the opposite-parity sites of in_j, the other parity zero,
+ * through the kernel the batched CG uses for D_oe p_j (one launch for all
+ * right-hand sides, reading the links once).  precision: colour-vector storage
+ * 32 or 16; FP32 links.  The launch shape is the autotuned one unless
+ * hisq_set_batched_kernel chose another. */
+hisq_status hisq_apply_dslash_batch(hisq_ctx *ctx, int out_parity, int precision, int nrhs, const double *in,
+                                    double *out);
+
+/* Launch shape of the batched operator (testing and tuning; kind 0 = autotuned,
+ * the default).  kind 1: one site per thread for rhs_per_thread (2..4)
+ * right-hand sides, links loaded by each thread, with (budget 0) or without
+ * (budget 1) an L2 prefetch of the next direction's links; kind 2: the same
+ * work split with the links of each site group and direction bulk-copied into
+ * a shared-memory ring, `budget` (2..4) blocks per SM (12-real long links only;
+ * never chosen by the autotuner, slower on GB300); kind 3: as kind 1 with the
+ * right-hand sides in pairs whose colour algebra runs as packed two-wide FP32
+ * FMAs (rhs_per_thread 2 or 4).  A shape that does not exist for a batch size
+ * makes the batched calls fail with HISQ_ERR_INVALID_ARG. */
+hisq_status hisq_set_batched_kernel(hisq_ctx *ctx, int kind, int rhs_per_thread, int budget);
+
 /* Even sites of `out` = (M^dag M)_ee applied to the even sites of `in`
  * (= 4m^2 in_e - D_eo D_oe in_e); odd sites of `out` are zero.  Precisions as
  * for hisq_apply_dslash. */
@@ -295,6 +317,15 @@ hisq_status hisq_set_profiling(hisq_ctx *ctx, int on);
  * call in progress returns HISQ_ERR_OOM with a message.  after < 0 switches the
  * injection off; the context stays usable.  Nothing is done on the device. */
 hisq_status hisq_inject_alloc_failure(hisq_ctx *ctx, int after);
+
+/* Failure injection of a bounded device wait (tests of the timeout path; the
+ * paper has no counterpart): with on != 0 the next tensor-core deflation
+ * (hisq_deflate_batch, or the batched solve's) launches its GEMM with a producer
+ * that issues no copy and with waits that give up after a few thousand polls,
+ * so the MMA warp's wait for its operands runs out while no copy and no MMA is
+ * in flight; the call returns HISQ_ERR_TIMEOUT with a message and the context
+ * stays usable.  One-shot: the next call runs normally.  on = 0 cancels it. */
+hisq_status hisq_inject_wait_timeout(hisq_ctx *ctx, int on);
 
 /* Bounds checking (a stand-in for a memory checker): in a library built with
  * -DHISQ_BOUNDS_CHECK every neighbour and site index is range-checked in the

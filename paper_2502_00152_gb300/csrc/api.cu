@@ -186,7 +186,7 @@ hisq_status hisq_create(const int dims[4], int t_antiperiodic, int device, void 
     *out = nullptr;
     long V = 1;
     for (int i = 0; i < 4; i++) {
-        if (dims[i] < 4 || dims[i] % 2) return HISQ_ERR_INVALID_ARG;
+        if (dims[i] < 4 || dims[i] % 2 || dims[i] >= (1 << 15)) return HISQ_ERR_INVALID_ARG;
         V *= dims[i];
     }
     if (V / 2 > (1L << 30)) return HISQ_ERR_INVALID_ARG;
@@ -205,6 +205,9 @@ hisq_status hisq_create(const int dims[4], int t_antiperiodic, int device, void 
     g.stride[1] = g.X;
     g.stride[2] = g.X * g.Y;
     g.stride[3] = g.X * g.Y * g.Z;
+    g.dX2 = make_fastdiv(g.X2);
+    g.dY = make_fastdiv(g.Y);
+    g.dZ = make_fastdiv(g.Z);
     auto fail = [&](hisq_status s) {
         hisq_destroy(ctx);
         return s;
@@ -243,6 +246,11 @@ hisq_status hisq_create(const int dims[4], int t_antiperiodic, int device, void 
                       cudaHostAllocMapped) != cudaSuccess)
         return fail(HISQ_ERR_OOM);
     if (cudaHostGetDevicePointer((void **)&ctx->bmonitor_d, ctx->bmonitor_h, 0) != cudaSuccess) return fail(HISQ_ERR_CUDA);
+    if (cudaHostAlloc((void **)&ctx->wait_status_h, sizeof(int), cudaHostAllocMapped) != cudaSuccess)
+        return fail(HISQ_ERR_OOM);
+    *ctx->wait_status_h = 0;
+    if (cudaHostGetDevicePointer((void **)&ctx->wait_status_d, ctx->wait_status_h, 0) != cudaSuccess)
+        return fail(HISQ_ERR_CUDA);
     // the fixed scratch of hisq_deflate_noalloc is reserved on this device now,
     // so that the no-allocation entry point itself never causes a reservation
     if (noalloc_scratch_address(ctx, nullptr) != HISQ_OK) return fail(HISQ_ERR_CUDA);
@@ -275,6 +283,7 @@ void hisq_destroy(hisq_ctx *ctx)
     cudaFree(ctx->bscal);
     cudaFree(ctx->bpartials);
     if (ctx->bmonitor_h) cudaFreeHost(ctx->bmonitor_h);
+    if (ctx->wait_status_h) cudaFreeHost(ctx->wait_status_h);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }
@@ -421,6 +430,62 @@ hisq_status hisq_inject_alloc_failure(hisq_ctx *ctx, int after)
 {
     if (!ctx) return HISQ_ERR_INVALID_ARG;
     ctx->alloc_fail_after = after < 0 ? -1 : after;
+    return HISQ_OK;
+}
+
+hisq_status hisq_set_batched_kernel(hisq_ctx *ctx, int kind, int rhs_per_thread, int budget)
+{
+    if (!ctx) return HISQ_ERR_INVALID_ARG;
+    if (kind < 0 || kind > 3) return set_err(ctx, HISQ_ERR_INVALID_ARG, "kind must be 0, 1, 2 or 3");
+    if (kind != 0 && (rhs_per_thread < 2 || rhs_per_thread > 4 || (kind == 3 && rhs_per_thread == 3)))
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "rhs_per_thread must be 2, 3 or 4 (2 or 4 for kind 3)");
+    if (((kind == 1 || kind == 3) && (budget < 0 || budget > 1)) || (kind == 2 && (budget < 2 || budget > 4)))
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "budget out of range for this kind");
+    ctx->mrhs_force_kind = kind;
+    ctx->mrhs_force_R = kind ? rhs_per_thread : 0;
+    ctx->mrhs_force_budget = kind ? budget : 0;
+    return HISQ_OK;
+}
+
+hisq_status hisq_apply_dslash_batch(hisq_ctx *ctx, int out_parity, int precision, int nrhs, const double *in,
+                                    double *out)
+{
+    if (!ctx) return HISQ_ERR_INVALID_ARG;
+    if (!in || !out || (out_parity != 0 && out_parity != 1) || nrhs < 1 || nrhs > kMaxBatch)
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "bad argument");
+    if (precision != 32 && precision != 16) return set_err(ctx, HISQ_ERR_INVALID_ARG, "precision must be 32 or 16");
+    if (!ctx->links_loaded) return set_err(ctx, HISQ_ERR_STATE, "links not loaded");
+    HISQ_CUDA(cudaSetDevice(ctx->device));
+    const int Vh = ctx->g.Vh;
+    const size_t sb = spinor_bytes(precision, Vh), full_bytes = size_t(ctx->g.V) * 48;
+    double *full = (double *)get_buf(ctx, BUF_TEST_A, full_bytes);
+    char *a = (char *)get_buf(ctx, BUF_B_P, sb * nrhs);
+    char *b = (char *)get_buf(ctx, BUF_B_TMP, sb * nrhs);
+    if (!full || !a || !b) return HISQ_ERR_OOM;
+    for (int j = 0; j < nrhs; j++) {
+        HISQ_CUDA(cudaMemcpyAsync(full, in + size_t(j) * ctx->g.V * 6, full_bytes, cudaMemcpyHostToDevice, ctx->stream));
+        TRY(launch_gather_parity(ctx, full, 1 - out_parity, precision, a + sb * j));
+    }
+    TRY(mrhs_set_identity(ctx, nrhs));
+    TRY(launch_mrhs_dslash_store(ctx, out_parity, precision, a, b, nrhs));
+    for (int j = 0; j < nrhs; j++) {
+        HISQ_CUDA(cudaMemsetAsync(full, 0, full_bytes, ctx->stream));
+        TRY(launch_scatter_parity(ctx, b + sb * j, precision, out_parity, full));
+        HISQ_CUDA(cudaMemcpyAsync(out + size_t(j) * ctx->g.V * 6, full, full_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+        HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    if (*(volatile int *)ctx->wait_status_h != 0) {
+        const int code = *ctx->wait_status_h;
+        *ctx->wait_status_h = 0;
+        return set_err(ctx, HISQ_ERR_TIMEOUT, "batched operator: a pipeline wait ran out (code %d)", code);
+    }
+    return HISQ_OK;
+}
+
+hisq_status hisq_inject_wait_timeout(hisq_ctx *ctx, int on)
+{
+    if (!ctx) return HISQ_ERR_INVALID_ARG;
+    ctx->inject_wait_timeout = on != 0;
     return HISQ_OK;
 }
 

@@ -381,6 +381,12 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
             upd = act;
         } else if (jj >= checked) {
             HISQ_CUDA(cudaEventSynchronize(ev[jj & 1]));
+            if (*(volatile int *)ctx->wait_status_h != 0) {
+                const int code = *ctx->wait_status_h;
+                cudaStreamSynchronize(ctx->stream);
+                *ctx->wait_status_h = 0;
+                return set_err(ctx, HISQ_ERR_TIMEOUT, "batched operator: a pipeline wait ran out (code %d)", code);
+            }
             retire(jj + 1);
             for (int j : act_at[jj & 3]) {
                 const double rr = ctx->bmonitor_h[size_t(jj % ctx->bmonitor_len) * kMaxBatch + j];

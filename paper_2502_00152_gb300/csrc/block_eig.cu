@@ -19,6 +19,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <complex>
 #include <numeric>
@@ -305,10 +306,23 @@ hisq_status block_trlm(hisq_ctx *ctx, const hisq_eig_params *P, int b, int n_ev,
     }
     std::vector<cd> H(size_t(n_kr) * n_kr, cd(0)), Rlast;
     int k = 0, conv = 0;
+    // phase times (logging only: the stream is synchronised at each boundary)
+    const bool timing = log_level() > 0;
+    double t_filter = 0, t_gs = 0, t_rr = 0, t_rot = 0;
+    auto t_last = std::chrono::steady_clock::now();
+    auto tick = [&](double &acc) {
+        if (!timing) return;
+        cudaStreamSynchronize(ctx->stream);
+        const auto now = std::chrono::steady_clock::now();
+        acc += std::chrono::duration<double>(now - t_last).count();
+        t_last = now;
+    };
     for (int restart = 0; restart <= P->max_restarts; restart++) {
         for (int j = k; j < n_kr; j += b) {
+            tick(t_rr);
             void *Wv = op_block(fld(j));
             if (!Wv) return HISQ_ERR_CUDA;
+            tick(t_filter);
             const int m = j + b;
             std::vector<cd> C;
             TRY_B(project_out((cuComplex *)Wv, m, C));
@@ -324,6 +338,7 @@ hisq_status block_trlm(hisq_ctx *ctx, const hisq_eig_params *P, int b, int n_ev,
                 Rlast = R;
             }
         }
+        tick(t_gs);
         // Rayleigh-Ritz: H Hermitian (mean of H and H^dag), eigenpairs on the device in FP64
         std::vector<cuDoubleComplex> Hh(H.size());
         for (int c = 0; c < n_kr; c++)
@@ -377,6 +392,7 @@ hisq_status block_trlm(hisq_ctx *ctx, const hisq_eig_params *P, int b, int n_ev,
                 Zh[size_t(c) * n_kr + r] = make_cuComplex(float(z.x), float(z.y));
             }
         HISQ_CUDA(cudaMemcpyAsync(Zd, Zh.data(), sizeof(cuComplex) * Zh.size(), cudaMemcpyHostToDevice, ctx->stream));
+        tick(t_rr);
         for (size_t r0 = 0; r0 < size_t(L); r0 += rot_rows) {
             const int len = int(std::min(rot_rows, size_t(L) - r0));
             BLAS(cublasCgemm(h.blas, CUBLAS_OP_N, CUBLAS_OP_N, len, nout, n_kr, &one, fld(0) + r0, L, Zd, n_kr, &zero, Td,
@@ -384,6 +400,10 @@ hisq_status block_trlm(hisq_ctx *ctx, const hisq_eig_params *P, int b, int n_ev,
             HISQ_CUDA(cudaMemcpy2DAsync(fld(0) + r0, sizeof(cuComplex) * L, Td, sizeof(cuComplex) * len,
                                         sizeof(cuComplex) * len, nout, cudaMemcpyDeviceToDevice, ctx->stream));
         }
+        tick(t_rot);
+        if (timing)
+            fprintf(stderr, "[hisq] block trlm times so far: filter %.2f s, Gram-Schmidt %.2f s, Rayleigh-Ritz %.2f s, "
+                            "rotation %.2f s\n", t_filter, t_gs, t_rr, t_rot);
         if (done) break;
         // thick restart: kept Ritz vectors, then the residual block V[n_kr .. n_kr+b)
         HISQ_CUDA(cudaMemcpyAsync(fld(n_keep), fld(n_kr), sf * b, cudaMemcpyDeviceToDevice, ctx->stream));

@@ -103,6 +103,26 @@ __device__ __forceinline__ void su3_third_row(CMat<T> &W)
 }
 
 // ---------------------------------------------------------------- geometry
+// Exact division of n < 2^31 by a constant d < 2^16 as a multiply and a
+// shift: with 2^s >= d and M = floor(2^(32+s) / d) + 1, floor(n M / 2^(32+s))
+// = floor(n / d), because the excess n (M - 2^(32+s)/d) / 2^(32+s) < 1/(2d)
+// never carries past the next multiple of 1/d (Granlund & Montgomery, PLDI 1994).
+struct FastDiv {
+    unsigned long long M;
+    int shift; // 32 + s
+    int d;
+};
+inline FastDiv make_fastdiv(int d)
+{
+    int s = 0;
+    while ((1 << s) < d) s++;
+    return FastDiv{((1ull << (32 + s)) / unsigned(d)) + 1ull, 32 + s, d};
+}
+__host__ __device__ __forceinline__ int fdiv(int n, const FastDiv &f)
+{
+    return int((unsigned long long)unsigned(n) * f.M >> f.shift);
+}
+
 struct Geom {
     int X, Y, Z, T;
     int X2;          // X / 2
@@ -111,6 +131,7 @@ struct Geom {
     int t_antiperiodic;
     int stride[4];   // 1, X, XY, XYZ (full-lattice site index)
     int *oob;        // device flag set by out-of-range indices (HISQ_BOUNDS_CHECK builds)
+    FastDiv dX2, dY, dZ; // division by X/2, Y and Z (site coordinates)
 };
 
 // Index check of the bounds-checking build (-DHISQ_BOUNDS_CHECK): an index
@@ -132,12 +153,14 @@ __device__ __forceinline__ int checked_index(const Geom &, int i, int) { return 
 // coordinates of checkerboard site cb of parity `par` (cb = s >> 1)
 __device__ __forceinline__ void cb_coords(const Geom &g, int par, int cb, int c[4])
 {
-    int xh = cb % g.X2;
-    int r = cb / g.X2;
-    c[1] = r % g.Y;
-    r /= g.Y;
-    c[2] = r % g.Z;
-    c[3] = r / g.Z;
+    int r = fdiv(cb, g.dX2);
+    const int xh = cb - r * g.X2;
+    int q = fdiv(r, g.dY);
+    c[1] = r - q * g.Y;
+    r = q;
+    q = fdiv(r, g.dZ);
+    c[2] = r - q * g.Z;
+    c[3] = q;
     c[0] = 2 * xh + ((par + c[1] + c[2] + c[3]) & 1);
 }
 
@@ -766,11 +789,21 @@ struct hisq_ctx {
     double *bmonitor_d = nullptr;
     int bmonitor_len = 4096;
 
+    // status word of the bounded waits in the pipelined kernels (host-mapped;
+    // non-zero: a wait ran out, the code says which)
+    int *wait_status_h = nullptr;
+    int *wait_status_d = nullptr;
+
     // host-side failure injection: allocations left before they fail (-1: off)
     long long alloc_fail_after = -1;
+    // host-side failure injection: the next tensor-core deflation issues no copy
+    // and gives up its waits after a few thousand polls (one-shot)
+    bool inject_wait_timeout = false;
 
     // launch shapes chosen by the autotuner, by problem key
     std::map<unsigned long long, int> tuned;
+    // a batched-operator launch shape chosen by the caller (0: autotuned)
+    int mrhs_force_kind = 0, mrhs_force_R = 0, mrhs_force_budget = 0;
 
     // scratch buffers (grown on demand)
     void *bufs[hisq::BUF_COUNT] = {};
@@ -922,6 +955,7 @@ hisq_status autotune(hisq_ctx *ctx, unsigned long long key, int n, int dflt, F &
             st = cuda_err(ctx, cudaGetLastError(), "tuner timing");
             break;
         }
+        if (log_level() > 1) fprintf(stderr, "[hisq] autotune key %llx: candidate %d: %.3f ms per launch\n", key, i, ms / 2);
         if (ms < best_ms) {
             best_ms = ms;
             best = i;
@@ -1008,6 +1042,7 @@ hisq_status launch_mrhs_p_update(hisq_ctx *ctx, int prec, void *r, void *p, int 
 hisq_status mrhs_set_identity(hisq_ctx *ctx, int k);
 hisq_status launch_mrhs_dslash_lin(hisq_ctx *ctx, int par, const void *in, void *out, double a, const void *x,
                                    double b, const void *y, double c, int k);
+hisq_status launch_mrhs_dslash_store(hisq_ctx *ctx, int par, int prec, const void *in, void *out, int k);
 
 // double-float operator (df64.cu): fields of HISQ_PREC_DF64 storage
 hisq_status ensure_df_links(hisq_ctx *ctx);

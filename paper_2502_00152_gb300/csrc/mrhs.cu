@@ -11,8 +11,12 @@
 #include <algorithm>
 #include <cstddef>
 #include <functional>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "internal.cuh"
+#include "tc.cuh"
 
 namespace hisq {
 
@@ -220,7 +224,10 @@ __device__ __forceinline__ void prefetch_long(const LinksF8 &L, int mu, int i)
     for (int k = 0; k < 4; k++) prefetch_l2(q + size_t(k) * L.Vh);
 }
 
-template <int R, class S, class Lk, class L12T, bool R12, class Epi>
+// PF: request the next direction's links into L2 while this one is computed
+// (15 prefetch instructions per thread and direction; the autotuner weighs them
+// against the latency they hide)
+template <int R, class S, class Lk, class L12T, bool R12, class Epi, bool PF = true>
 __global__ void __launch_bounds__(512, 1)
     k_dslash_mrhs(Geom g, int par, Lk L, L12T L12, float c3, BatchF<S> in, const BatchScalars *scal, MrhsTile tl,
                   Epi epi, BatchRed br)
@@ -255,7 +262,7 @@ __global__ void __launch_bounds__(512, 1)
             const int f3 = nb_cb(g, c, s, mu, +3), b3 = nb_cb(g, c, s, mu, -3);
             // the next direction's links (read from DRAM once per launch) are
             // requested into L2 while this direction is computed
-            if (mu < 3) {
+            if (PF && mu < 3) {
                 L.prefetch(mu + 1, cb);
                 prefetch_long(L12, mu + 1, cb);
             }
@@ -337,6 +344,390 @@ __global__ void __launch_bounds__(512, 1)
     batch_reduce<R>(red, tl, kact, br);
 }
 
+// ------------------------------------------------- packed FP32 pairs
+// Blackwell executes two FP32 FMAs of a register pair in one instruction
+// (fma.rn.f32x2: each half is an IEEE fused multiply-add, the same result as
+// two scalar ones).  The packed kernel carries right-hand sides in pairs, so
+// the colour algebra of two right-hand sides issues as one instruction stream:
+// with the link entries broadcast to both halves, a complex multiply-add of a
+// pair is four packed FMAs instead of eight scalar ones.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+// a colour vector of two right-hand sides: (re, im) of each colour as pairs,
+// and -im for the real part of the complex products
+struct CVec2 {
+    float2 re[3], im[3], nim[3];
+};
+struct CAcc2 {
+    float2 re[3], im[3];
+    __device__ __forceinline__ void zero()
+    {
+#pragma unroll
+        for (int c = 0; c < 3; c++) re[c] = im[c] = make_float2(0.f, 0.f);
+    }
+};
+
+template <class S>
+__device__ __forceinline__ CVec2 load_pair(const S &a, const S &b, int i)
+{
+    const CVec<float> x = a.load(i), y = b.load(i);
+    CVec2 v;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        v.re[c] = make_float2(x.re[c], y.re[c]);
+        v.im[c] = make_float2(x.im[c], y.im[c]);
+        v.nim[c] = make_float2(-x.im[c], -y.im[c]);
+    }
+    return v;
+}
+// FP16 storage: the per-site scales of the two right-hand sides are applied
+// as packed multiplies
+template <>
+__device__ __forceinline__ CVec2 load_pair<SpinorH>(const SpinorH &a, const SpinorH &b, int i)
+{
+    const uint4 ua = a.p[i], ub = b.p[i];
+    const float2 s2 = make_float2(__uint_as_float(ua.w), __uint_as_float(ub.w));
+    const float2 n2 = make_float2(-s2.x, -s2.y);
+    const unsigned ha[3] = {ua.x, ua.y, ua.z}, hb[3] = {ub.x, ub.y, ub.z};
+    CVec2 v;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float2 fa = __half22float2(*reinterpret_cast<const __half2 *>(&ha[c]));
+        const float2 fb = __half22float2(*reinterpret_cast<const __half2 *>(&hb[c]));
+        const float2 re = make_float2(fa.x, fb.x), im = make_float2(fa.y, fb.y);
+        v.re[c] = mul2(re, s2);
+        v.im[c] = mul2(im, s2);
+        v.nim[c] = mul2(im, n2);
+    }
+    return v;
+}
+
+// acc += W v for a pair (W shared by both)
+__device__ __forceinline__ void mv_acc2(CAcc2 &acc, const CMat<float> &W, const CVec2 &v)
+{
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            const float2 wr = make_float2(W.re[3 * i + j], W.re[3 * i + j]);
+            const float2 wi = make_float2(W.im[3 * i + j], W.im[3 * i + j]);
+            acc.re[i] = fma2(wr, v.re[j], acc.re[i]);
+            acc.re[i] = fma2(wi, v.nim[j], acc.re[i]);
+            acc.im[i] = fma2(wr, v.im[j], acc.im[i]);
+            acc.im[i] = fma2(wi, v.re[j], acc.im[i]);
+        }
+}
+// acc += s (W v), s real
+__device__ __forceinline__ void mv_acc2_scaled(CAcc2 &acc, float s, const CMat<float> &W, const CVec2 &v)
+{
+    CAcc2 t;
+    t.zero();
+    mv_acc2(t, W, v);
+    const float2 s2 = make_float2(s, s);
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        acc.re[i] = fma2(s2, t.re[i], acc.re[i]);
+        acc.im[i] = fma2(s2, t.im[i], acc.im[i]);
+    }
+}
+
+// The batched operator with P pairs (R = 2P right-hand sides) per thread;
+// tiling, masking and reductions as k_dslash_mrhs.
+template <int P, class S, class Lk, class L12T, bool R12, class Epi, bool PF>
+__global__ void __launch_bounds__(512, 1)
+    k_dslash_mrhs_x2(Geom g, int par, Lk L, L12T L12, float c3, BatchF<S> in, const BatchScalars *scal, MrhsTile tl,
+                     Epi epi, BatchRed br)
+{
+    constexpr int R = 2 * P;
+    const int kact = scal->kact;
+    int jj[R];
+    bool on[R];
+#pragma unroll
+    for (int u = 0; u < R; u++) {
+        const int q = tl.chunk() * R + u;
+        on[u] = q < kact;
+        jj[u] = scal->idx[on[u] ? q : kact - 1];
+    }
+    double red[R];
+#pragma unroll
+    for (int u = 0; u < R; u++) red[u] = 0;
+    const int step = gridDim.x * tl.nsg * 32;
+    for (int cb = (blockIdx.x * tl.nsg + tl.group()) * 32 + (threadIdx.x & 31); cb < g.Vh; cb += step) {
+        int c[4];
+        cb_coords(g, par, cb, c);
+        const int s = full_site(g, c);
+        CAcc2 acc[P];
+#pragma unroll
+        for (int q = 0; q < P; q++) acc[q].zero();
+#pragma unroll 1
+        for (int mu = 0; mu < 4; mu++) {
+            const int f1 = nb_cb(g, c, s, mu, +1), b1 = nb_cb(g, c, s, mu, -1);
+            const int f3 = nb_cb(g, c, s, mu, +3), b3 = nb_cb(g, c, s, mu, -3);
+            if (PF && mu < 3) {
+                L.prefetch(mu + 1, cb);
+                prefetch_long(L12, mu + 1, cb);
+            }
+            CMat<float> f, b;
+            L.load(mu, 0, cb, f, b);
+#pragma unroll
+            for (int q = 0; q < P; q++) {
+                const S va = in.at(jj[2 * q]), vb = in.at(jj[2 * q + 1]);
+                mv_acc2(acc[q], f, load_pair(va, vb, f1));
+                mv_acc2(acc[q], b, load_pair(va, vb, b1));
+            }
+            if constexpr (R12) {
+                CMat<float> f3m, b3m;
+                L12.load(mu, cb, f3m, b3m);
+                const float eta = stag_phase(mu, c);
+                float sf = eta * c3, sb = -eta * c3;
+                if (mu == 3 && g.t_antiperiodic) {
+                    if (c[3] + 3 >= g.T) sf = -sf;
+                    if (c[3] < 3) sb = -sb;
+                }
+#pragma unroll
+                for (int q = 0; q < P; q++) {
+                    const S va = in.at(jj[2 * q]), vb = in.at(jj[2 * q + 1]);
+                    mv_acc2_scaled(acc[q], sf, f3m, load_pair(va, vb, f3));
+                    mv_acc2_scaled(acc[q], sb, b3m, load_pair(va, vb, b3));
+                }
+            } else {
+                L.load(mu, 1, cb, f, b);
+#pragma unroll
+                for (int q = 0; q < P; q++) {
+                    const S va = in.at(jj[2 * q]), vb = in.at(jj[2 * q + 1]);
+                    mv_acc2(acc[q], f, load_pair(va, vb, f3));
+                    mv_acc2(acc[q], b, load_pair(va, vb, b3));
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < P; q++) {
+            CVec<float> x, y;
+#pragma unroll
+            for (int i = 0; i < 3; i++) {
+                x.re[i] = acc[q].re[i].x;
+                x.im[i] = acc[q].im[i].x;
+                y.re[i] = acc[q].re[i].y;
+                y.im[i] = acc[q].im[i].y;
+            }
+            if (on[2 * q]) epi(cb, jj[2 * q], x, red[2 * q]);
+            if (on[2 * q + 1]) epi(cb, jj[2 * q + 1], y, red[2 * q + 1]);
+        }
+    }
+    batch_reduce<R>(red, tl, kact, br);
+}
+
+// ------------------------------------------------- the TMA-fed batched kernel
+// The same operator with the links of each (site group, direction) copied into
+// shared memory by the bulk-copy engine (one elected thread per site group
+// issues 15 copies of 512 B: the 9 fat rows and the 6 stored long rows of 32
+// consecutive sites) into a ring of `stages` slots guarded by mbarriers.  The
+// warps then read each link element from shared memory once per R right-hand
+// sides, so no link load is held in registers while the DRAM latency elapses:
+// registers go to accumulators and neighbour gathers, and more warps fit.  The
+// third row of each long link is rebuilt on the fly from the two stored rows,
+// with the staggered phase, boundary sign and c3 applied to the rows first
+// (row 2 of s*S is conj(s a x s b) / s).  Every wait is bounded: a wait that
+// runs out records its code in *status and the warp gives up on the rest of its
+// items (the reduction still runs, so the launch ends).
+constexpr int kTmaRows = 15;                 // 9 fat + 6 long rows per (site group, direction)
+constexpr int kTmaStageBytes = kTmaRows * 512; // 32 sites x float4 per row
+
+template <int R, class S, class Epi, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+    k_dslash_mrhs_tma(Geom g, int par, const float4 *__restrict__ fat, const float4 *__restrict__ lng, float c3,
+                      float inv_c3, BatchF<S> in, const BatchScalars *scal, MrhsTile tl, Epi epi, BatchRed br,
+                      int stages, int *status)
+{
+    extern __shared__ __align__(128) unsigned char dsm[];
+    const int grp = tl.group(), chk = tl.chunk(), lane = threadIdx.x & 31;
+    unsigned char *ring = dsm + size_t(grp) * stages * kTmaStageBytes;
+    uint64_t *full = reinterpret_cast<uint64_t *>(dsm + size_t(tl.nsg) * stages * kTmaStageBytes) + 2 * grp * stages;
+    uint64_t *empty = full + stages;
+    const bool producer = chk == 0 && lane == 0;
+    if (producer) {
+        for (int q = 0; q < stages; q++) {
+            tc::mbar_init(&full[q], 1);
+            tc::mbar_init(&empty[q], tl.nch);
+        }
+        tc::fence_mbar_init();
+    }
+    __syncthreads();
+
+    const int kact = scal->kact;
+    int jj[R];
+    bool on[R];
+#pragma unroll
+    for (int u = 0; u < R; u++) {
+        const int q = chk * R + u;
+        on[u] = q < kact;
+        jj[u] = scal->idx[on[u] ? q : kact - 1];
+    }
+    double red[R];
+#pragma unroll
+    for (int u = 0; u < R; u++) red[u] = 0;
+
+    const int Vh = g.Vh;
+    const int ngroups = (Vh + 31) / 32;
+    const int first = blockIdx.x * tl.nsg + grp, gstride = gridDim.x * tl.nsg;
+    const int nitems = first < ngroups ? ((ngroups - 1 - first) / gstride + 1) * 4 : 0;
+    // item j = (site-group iteration j / 4, direction j % 4) into slot j % stages
+    auto issue = [&](int j) {
+        const int mu = j & 3;
+        const int cb0 = (first + (j >> 2) * gstride) * 32;
+        const uint32_t rb = uint32_t(min(32, Vh - cb0)) * 16u;
+        uint64_t *fb = &full[j % stages];
+        unsigned char *st = ring + size_t(j % stages) * kTmaStageBytes;
+        tc::mbar_arrive_expect_tx(fb, kTmaRows * rb);
+#pragma unroll 1
+        for (int k = 0; k < 9; k++) tc::bulk_load_1d(st + k * 512, fat + size_t(mu * 9 + k) * Vh + cb0, rb, fb);
+#pragma unroll 1
+        for (int k = 0; k < 6; k++) tc::bulk_load_1d(st + (9 + k) * 512, lng + size_t(mu * 6 + k) * Vh + cb0, rb, fb);
+    };
+    int issued = 0;
+    if (producer)
+        for (; issued < min(stages - 1, nitems); issued++) issue(issued);
+
+    bool ok = true;
+    CVec<float> acc[R];
+    int c[4] = {0, 0, 0, 0}, s = 0, cb = 0;
+    bool valid = false;
+#pragma unroll 1
+    for (int it = 0; it < nitems; it++) {
+        const int mu = it & 3;
+        if (producer) {
+            // keep up to `stages` items in flight; a slot is refilled once every
+            // warp of the group has released it, and the producer blocks only
+            // when the item its own warp needs next has not been issued yet
+            while (ok && issued < nitems && issued < it + stages) {
+                if (issued >= stages) {
+                    const uint32_t par_e = ((issued / stages) - 1) & 1;
+                    if (!tc::mbar_try_wait(&empty[issued % stages], par_e)) {
+                        if (issued > it) break; // not needed yet: try again at the next item
+                        ok = tc::mbar_wait(&empty[issued % stages], par_e, status, tc::TC_TIMEOUT_EMPTY);
+                        if (!ok) break;
+                    }
+                }
+                issue(issued++);
+            }
+        }
+        if (!ok) break;
+        if (mu == 0) {
+            cb = (first + (it >> 2) * gstride) * 32 + lane;
+            valid = cb < Vh;
+            cb_coords(g, par, valid ? cb : Vh - 1, c);
+            s = full_site(g, c);
+#pragma unroll
+            for (int u = 0; u < R; u++) acc[u].zero();
+        }
+        // the neighbour gathers do not depend on the links: issue them before
+        // waiting for the slot, so their latency overlaps the copies'
+        const int f1 = nb_cb(g, c, s, mu, +1), b1 = nb_cb(g, c, s, mu, -1);
+        const int f3 = nb_cb(g, c, s, mu, +3), b3 = nb_cb(g, c, s, mu, -3);
+        CVec<float> v[4][R];
+#pragma unroll
+        for (int u = 0; u < R; u++) {
+            const S f = in.at(jj[u]);
+            v[0][u] = cvt<float>(f.load(f1));
+            v[1][u] = cvt<float>(f.load(b1));
+            v[2][u] = cvt<float>(f.load(f3));
+            v[3][u] = cvt<float>(f.load(b3));
+        }
+        if (!tc::mbar_wait(&full[it % stages], (it / stages) & 1, status, tc::TC_TIMEOUT_FULL)) {
+            ok = false;
+            break;
+        }
+        const float4 *rows = reinterpret_cast<const float4 *>(ring + size_t(it % stages) * kTmaStageBytes) + lane;
+        // fat links: forward (x, y of each row element) and backward (z, w)
+#pragma unroll
+        for (int d = 0; d < 2; d++) {
+#pragma unroll
+            for (int k = 0; k < 9; k++) {
+                const float2 w = d == 0 ? *reinterpret_cast<const float2 *>(rows + 32 * k)
+                                        : *(reinterpret_cast<const float2 *>(rows + 32 * k) + 1);
+                const int i = k / 3, j = k % 3;
+#pragma unroll
+                for (int u = 0; u < R; u++) {
+                    acc[u].re[i] = fmaf(w.x, v[d][u].re[j], fmaf(-w.y, v[d][u].im[j], acc[u].re[i]));
+                    acc[u].im[i] = fmaf(w.x, v[d][u].im[j], fmaf(w.y, v[d][u].re[j], acc[u].im[i]));
+                }
+            }
+        }
+        // long links: rows a, b of the SU(3) factor times the hop's sign s,
+        // row 2 = conj(s a x s b) / s
+        const float eta = stag_phase(mu, c);
+        float sgn[2] = {eta, -eta};
+        if (mu == 3 && g.t_antiperiodic) {
+            if (c[3] + 3 >= g.T) sgn[0] = -sgn[0];
+            if (c[3] < 3) sgn[1] = -sgn[1];
+        }
+#pragma unroll
+        for (int d = 0; d < 2; d++) {
+            const float sc = sgn[d] * c3, isc = sgn[d] * inv_c3;
+            float ar[6], ai[6]; // rows 0 and 1: (a0, a1, a2, b0, b1, b2)
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                const float2 w = d == 0 ? *reinterpret_cast<const float2 *>(rows + 32 * (9 + k))
+                                        : *(reinterpret_cast<const float2 *>(rows + 32 * (9 + k)) + 1);
+                ar[k] = sc * w.x;
+                ai[k] = sc * w.y;
+                const int i = k / 3, j = k % 3;
+#pragma unroll
+                for (int u = 0; u < R; u++) {
+                    acc[u].re[i] = fmaf(ar[k], v[2 + d][u].re[j], fmaf(-ai[k], v[2 + d][u].im[j], acc[u].re[i]));
+                    acc[u].im[i] = fmaf(ar[k], v[2 + d][u].im[j], fmaf(ai[k], v[2 + d][u].re[j], acc[u].im[i]));
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                // (a x b)_j = a_{j+1} b_{j+2} - a_{j+2} b_{j+1}; row 2 entry = conj(.) / s
+                const int j1 = (j + 1) % 3, j2 = (j + 2) % 3;
+                const float xr = (ar[j1] * ar[3 + j2] - ai[j1] * ai[3 + j2]) - (ar[j2] * ar[3 + j1] - ai[j2] * ai[3 + j1]);
+                const float xi = (ar[j1] * ai[3 + j2] + ai[j1] * ar[3 + j2]) - (ar[j2] * ai[3 + j1] + ai[j2] * ar[3 + j1]);
+                const float wr = xr * isc, wi = -xi * isc;
+#pragma unroll
+                for (int u = 0; u < R; u++) {
+                    acc[u].re[2] = fmaf(wr, v[2 + d][u].re[j], fmaf(-wi, v[2 + d][u].im[j], acc[u].re[2]));
+                    acc[u].im[2] = fmaf(wr, v[2 + d][u].im[j], fmaf(wi, v[2 + d][u].re[j], acc[u].im[2]));
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&empty[it % stages]);
+        if (mu == 3 && valid) {
+#pragma unroll
+            for (int u = 0; u < R; u++)
+                if (on[u]) epi(cb, jj[u], acc[u], red[u]);
+        }
+    }
+    // copies still in flight (only after a wait gave up) land before the CTA exits
+    if (producer && !ok) {
+        for (int j = max(0, issued - stages); j < issued; j++)
+            for (int spin = 0; spin < (1 << 20) && !tc::mbar_try_wait(&full[j % stages], (j / stages) & 1); spin++) {
+            }
+    }
+    batch_reduce<R>(red, tl, kact, br);
+}
+
 // ------------------------------------------------------------- launch glue
 // Launch shapes of the batched kernels, tried by the autotuner on the first
 // D_oe launch of each (batch size, precision, link format): R right-hand
@@ -346,23 +737,54 @@ __global__ void __launch_bounds__(512, 1)
 struct MrhsShape {
     int R;
     MrhsTile tile;
+    int rc;  // k_dslash_mrhs: 0 with the L2 link prefetch, 1 without; k_dslash_mrhs_tma: blocks per SM
+    int tma; // 1: the TMA-fed kernel (FP32 links with 12-real long links only)
+    int x2;  // 1: the packed-pair kernel (R even)
 };
+constexpr int kTmaStages = 4;
 
-static int mrhs_candidates(int kact, MrhsShape *out)
+constexpr int kMaxMrhsCandidates = 40;
+
+// Candidates the autotuner times: the register kernel with R = 4, 3, 2 right-hand
+// sides per thread, one or two site-group counts per block, with and without
+// the link prefetch.  With `all` it also lists the packed-pair kernel and the
+// TMA-fed kernel (12-real long links), which run only when a caller selects
+// them: both measured slower on GB300 (packed FMAs save issue slots but take
+// two FMA-pipe cycles each, and both hold fewer warps per SM at 128 registers).
+static int mrhs_candidates(int kact, MrhsShape *out, bool tma_ok, bool all)
 {
     int n = 0;
-    for (int R : {4, 3, 2}) {
-        const int nch = (kact + R - 1) / R;
-        if (nch > 16) continue;
-        const int nsg0 = std::max(1, 8 / nch);
-        for (int nsg : {nsg0, 2 * nsg0}) {
-            if (32 * nch * nsg > 512 || nsg > 8) continue; // batch_reduce holds 8 site groups
+    for (int x2 : {0, 1})
+        for (int pf : {0, 1})
+            for (int R : {4, 3, 2}) {
+                if (x2 && (R % 2 || !all)) continue;
+                const int nch = (kact + R - 1) / R;
+                if (nch > 16) continue;
+                const int nsg0 = std::max(1, 8 / nch);
+                for (int nsg : {nsg0, 2 * nsg0}) {
+                    if (32 * nch * nsg > 512 || nsg > 8) continue; // batch_reduce holds 8 site groups
+                    out[n].R = R;
+                    out[n].tile.nch = nch;
+                    out[n].tile.nsg = nsg;
+                    out[n].rc = pf;
+                    out[n].tma = 0;
+                    out[n].x2 = x2;
+                    n++;
+                }
+            }
+    if (!all || !tma_ok) return n;
+    for (int minb : {2, 3, 4})
+        for (int R : {4, 3, 2}) {
+            const int nch = (kact + R - 1) / R;
+            if (32 * nch > 256 || n >= kMaxMrhsCandidates) continue;
             out[n].R = R;
             out[n].tile.nch = nch;
-            out[n].tile.nsg = nsg;
+            out[n].tile.nsg = std::min(8, std::max(1, 256 / (32 * nch)));
+            out[n].rc = minb;
+            out[n].tma = 1;
+            out[n].x2 = 0;
             n++;
         }
-    }
     return n;
 }
 
@@ -414,8 +836,33 @@ struct LinksFvB {
     }
 };
 
+template <int P, class S, class Epi>
+static hisq_status run_mrhs_x2(hisq_ctx *ctx, int par, const BatchF<S> &in, const MrhsTile &tl, int pf, const Epi &epi,
+                               BatchRed br)
+{
+    const int Vh = ctx->g.Vh;
+    const int threads = 32 * tl.nch * tl.nsg;
+    LinksFvB L{ctx->links_f[par], Vh, ctx->long_recon == 18 ? 2 : 1};
+    auto launch = [&](auto kern, auto L12) -> hisq_status {
+        const int grid = grid_for(ctx, long(Vh), 32 * tl.nsg, mrhs_blocks_per_sm(kern, threads));
+        kern<<<grid, threads, 0, ctx->stream>>>(ctx->g, par, L, L12, float(ctx->long_scale), in, ctx->bscal, tl, epi,
+                                               br);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_err(ctx, e, "batched dslash (packed) launch");
+        return HISQ_OK;
+    };
+    if (ctx->long_recon == 12) {
+        const LinksF12 l12{ctx->links_f12[par], Vh};
+        if (pf == 1) return launch(k_dslash_mrhs_x2<P, S, LinksFvB, LinksF12, true, Epi, false>, l12);
+        return launch(k_dslash_mrhs_x2<P, S, LinksFvB, LinksF12, true, Epi, true>, l12);
+    }
+    if (ctx->long_recon == 8)
+        return launch(k_dslash_mrhs_x2<P, S, LinksFvB, LinksF8, true, Epi, true>, LinksF8{ctx->links_f12[par], Vh});
+    return launch(k_dslash_mrhs_x2<P, S, LinksFvB, LinksF12, false, Epi, true>, LinksF12{nullptr, Vh});
+}
+
 template <int R, class S, class Epi>
-static hisq_status run_mrhs_r(hisq_ctx *ctx, int par, const BatchF<S> &in, const MrhsTile &tl, const Epi &epi,
+static hisq_status run_mrhs_r(hisq_ctx *ctx, int par, const BatchF<S> &in, const MrhsTile &tl, int rc, const Epi &epi,
                               BatchRed br)
 {
     const int Vh = ctx->g.Vh;
@@ -429,21 +876,81 @@ static hisq_status run_mrhs_r(hisq_ctx *ctx, int par, const BatchF<S> &in, const
         if (e != cudaSuccess) return cuda_err(ctx, e, "batched dslash launch");
         return HISQ_OK;
     };
-    if (ctx->long_recon == 12)
-        return launch(k_dslash_mrhs<R, S, LinksFvB, LinksF12, true, Epi>, LinksF12{ctx->links_f12[par], Vh});
+    if (ctx->long_recon == 12) {
+        const LinksF12 l12{ctx->links_f12[par], Vh};
+        if (rc == 1) return launch(k_dslash_mrhs<R, S, LinksFvB, LinksF12, true, Epi, false>, l12);
+        return launch(k_dslash_mrhs<R, S, LinksFvB, LinksF12, true, Epi>, l12);
+    }
     if (ctx->long_recon == 8)
         return launch(k_dslash_mrhs<R, S, LinksFvB, LinksF8, true, Epi>, LinksF8{ctx->links_f12[par], Vh});
     return launch(k_dslash_mrhs<R, S, LinksFvB, LinksF12, false, Epi>, LinksF12{nullptr, Vh});
+}
+
+// dynamic shared memory of the TMA-fed kernel for a tile: the slot rings and
+// two mbarriers per slot, per site group
+static size_t tma_smem_bytes(const MrhsTile &tl)
+{
+    return size_t(tl.nsg) * kTmaStages * (kTmaStageBytes + 2 * sizeof(uint64_t));
+}
+
+template <int R, class S, class Epi>
+static hisq_status run_mrhs_tma(hisq_ctx *ctx, int par, const BatchF<S> &in, const MrhsTile &tl, int minb,
+                                const Epi &epi, BatchRed br)
+{
+    const int Vh = ctx->g.Vh;
+    const int threads = 32 * tl.nch * tl.nsg;
+    const size_t smem = tma_smem_bytes(tl);
+    auto launch = [&](auto kern) -> hisq_status {
+        static std::mutex mu;
+        static std::map<std::pair<const void *, size_t>, int> bps_cache; // (kernel, smem) -> blocks per SM
+        int bps = 1;
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            const auto key = std::make_pair(reinterpret_cast<const void *>(kern), smem * 1024 + size_t(threads));
+            auto itc = bps_cache.find(key);
+            if (itc == bps_cache.end()) {
+                HISQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+                int n = 0;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, threads, smem) != cudaSuccess || n < 1) {
+                    cudaGetLastError();
+                    n = 1;
+                }
+                itc = bps_cache.emplace(key, n).first;
+            }
+            bps = itc->second;
+        }
+        const int grid = grid_for(ctx, long(Vh), 32 * tl.nsg, bps);
+        kern<<<grid, threads, smem, ctx->stream>>>(ctx->g, par, ctx->links_f[par], ctx->links_f12[par],
+                                                   float(ctx->long_scale), float(1.0 / ctx->long_scale), in,
+                                                   ctx->bscal, tl, epi, br, kTmaStages, ctx->wait_status_d);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_err(ctx, e, "batched dslash (TMA) launch");
+        return HISQ_OK;
+    };
+    if (minb == 3) return launch(k_dslash_mrhs_tma<R, S, Epi, 3>);
+    if (minb == 4) return launch(k_dslash_mrhs_tma<R, S, Epi, 4>);
+    return launch(k_dslash_mrhs_tma<R, S, Epi, 2>);
 }
 
 template <class S, class Epi>
 static hisq_status run_shape(hisq_ctx *ctx, int par, const BatchF<S> &in, const MrhsShape &sh, const Epi &epi,
                              BatchRed br)
 {
+    if (sh.x2) {
+        if (sh.R == 4) return run_mrhs_x2<2>(ctx, par, in, sh.tile, sh.rc, epi, br);
+        return run_mrhs_x2<1>(ctx, par, in, sh.tile, sh.rc, epi, br);
+    }
+    if (sh.tma) {
+        switch (sh.R) {
+        case 2: return run_mrhs_tma<2>(ctx, par, in, sh.tile, sh.rc, epi, br);
+        case 3: return run_mrhs_tma<3>(ctx, par, in, sh.tile, sh.rc, epi, br);
+        default: return run_mrhs_tma<4>(ctx, par, in, sh.tile, sh.rc, epi, br);
+        }
+    }
     switch (sh.R) {
-    case 2: return run_mrhs_r<2>(ctx, par, in, sh.tile, epi, br);
-    case 3: return run_mrhs_r<3>(ctx, par, in, sh.tile, epi, br);
-    default: return run_mrhs_r<4>(ctx, par, in, sh.tile, epi, br);
+    case 2: return run_mrhs_r<2>(ctx, par, in, sh.tile, sh.rc, epi, br);
+    case 3: return run_mrhs_r<3>(ctx, par, in, sh.tile, sh.rc, epi, br);
+    default: return run_mrhs_r<4>(ctx, par, in, sh.tile, sh.rc, epi, br);
     }
 }
 
@@ -452,9 +959,23 @@ static hisq_status run_shape(hisq_ctx *ctx, int par, const BatchF<S> &in, const 
 static hisq_status mrhs_shape(hisq_ctx *ctx, int kact, int prec, MrhsShape *sh, bool may_tune,
                               const std::function<hisq_status(const MrhsShape &)> &launch)
 {
-    MrhsShape cand[16];
-    const int n = mrhs_candidates(kact, cand);
+    MrhsShape cand[kMaxMrhsCandidates];
+    const bool forced = ctx->mrhs_force_kind != 0;
+    const int n = mrhs_candidates(kact, cand, ctx->long_recon == 12, forced);
     int idx = 0;
+    if (forced) {
+        // a launch shape chosen by the caller (hisq_set_batched_kernel)
+        for (int i = 0; i < n; i++)
+            if (cand[i].tma == (ctx->mrhs_force_kind == 2) && cand[i].x2 == (ctx->mrhs_force_kind == 3) &&
+                cand[i].R == ctx->mrhs_force_R && cand[i].rc == ctx->mrhs_force_budget) {
+                *sh = cand[i];
+                return HISQ_OK;
+            }
+        return set_err(ctx, HISQ_ERR_INVALID_ARG,
+                       "batched operator: no launch shape of kind %d with %d right-hand sides per thread and budget %d "
+                       "for %d right-hand sides and these links",
+                       ctx->mrhs_force_kind, ctx->mrhs_force_R, ctx->mrhs_force_budget, kact);
+    }
     const unsigned long long key = mrhs_key(ctx, kact, prec);
     if (may_tune) {
         hisq_status st = autotune(ctx, key, n, 0, [&](int i) { return launch(cand[i]); }, &idx);
@@ -525,6 +1046,23 @@ hisq_status launch_mrhs_dslash_update(hisq_ctx *ctx, int prec, int link_prec, vo
     }
     }
     return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched sloppy precision must be 32 or 16");
+}
+
+// out_j = D in_j on output parity par for the k fields of a block (slots
+// 0..k-1 active, mrhs_set_identity), FP32 or FP16 storage; |out_j|^2 -> out[j]
+hisq_status launch_mrhs_dslash_store(hisq_ctx *ctx, int par, int prec, const void *in, void *out, int k)
+{
+    const int Vh = ctx->g.Vh;
+    BatchRed br = batch_red(ctx, BFIN_STORE);
+    switch (prec) {
+    case 32:
+        return run_mrhs(ctx, par, 32, 32, batchf<SpinorF>(const_cast<void *>(in), Vh, 32), k,
+                        BEpiStore<SpinorF>{batchf<SpinorF>(out, Vh, 32)}, br, false);
+    case 16:
+        return run_mrhs(ctx, par, 32, 16, batchf<SpinorH>(const_cast<void *>(in), Vh, 16), k,
+                        BEpiStore<SpinorH>{batchf<SpinorH>(out, Vh, 16)}, br, false);
+    }
+    return set_err(ctx, HISQ_ERR_INVALID_ARG, "batched operator: precision must be 32 or 16");
 }
 
 // active slots 0..k-1 = right-hand sides 0..k-1 (a block of ordinary fields)

@@ -56,9 +56,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 
 // bounded wait; returns false (and records `code` in *status) on timeout, and
 // at once when another thread of the grid has already given up
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status, int code)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status, int code,
+                                          uint32_t limit = kSpinLimit)
 {
-    for (uint32_t i = 0; i < kSpinLimit; i++) {
+    for (uint32_t i = 0; i < limit; i++) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 1023) == 1023 && *reinterpret_cast<volatile int *>(status) != TC_OK) return false;
     }
@@ -74,6 +75,16 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, uint64_
             smem_addr(dst)),
         "l"(tmap), "r"(smem_addr(bar)), "r"(x), "r"(y)
         : "memory");
+}
+
+// 1D bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from global to shared memory, completion counted on `bar`
+__device__ __forceinline__ void bulk_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
 }
 
 __device__ __forceinline__ void prefetch_tmap(const void *tmap)

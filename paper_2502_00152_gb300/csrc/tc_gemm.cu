@@ -89,6 +89,8 @@ static bool make_tmap(CUtensorMap *tm, const void *base, uint64_t inner, uint64_
 //   mode 1 (expansion):  persistent over row tiles (MT = 1), full K range; the
 //            epilogue applies the result to the right-hand-side fields.
 struct ExpandEpi {
+    uint32_t spin_limit; // polls of a bounded wait before it gives up
+    int no_loads;     // failure injection (tests): the producer issues no copy
     double2 *x;       // k FP64 even fields, element s of field j at x + j*xs + s
     double2 *r;       // nullptr: x only (the caller recomputes r = b - A x)
     size_t fstride;   // double2 elements between fields
@@ -163,7 +165,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     const int nk = (kend - kbeg + TC_BK - 1) / TC_BK;
 
-    if (warp == 0 && lane == 0) {
+    const uint32_t lim = epi.spin_limit;
+    if (warp == 0 && lane == 0 && !epi.no_loads) {
         // ---------------- TMA producer
         tc::prefetch_tmap(&tmAh);
         if (AK == AK_F16_SPLIT) tc::prefetch_tmap(&tmAl);
@@ -174,7 +177,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int m0 = (MODE == 0) ? t * MT * 128 : t * 128;
             for (int kk = 0; kk < nk; kk++, it++) {
                 const int s = it % STAGES;
-                if (it >= STAGES && !tc::mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, status, tc::TC_TIMEOUT_EMPTY))
+                if (it >= STAGES && !tc::mbar_wait(&empty[s], ((it / STAGES) - 1) & 1, status, tc::TC_TIMEOUT_EMPTY, lim))
                     goto producer_done;
                 uint8_t *st = smem + s * STAGE;
                 tc::mbar_arrive_expect_tx(&full[s], STAGE);
@@ -198,11 +201,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---------------- MMA issuer
         uint32_t it = 0, tcount = 0;
         for (int t = tile0; t < (MODE == 0 ? tile0 + 1 : ntiles); t += tstride, tcount++) {
-            if (tcount > 0 && !tc::mbar_wait(drained, (tcount - 1) & 1, status, tc::TC_TIMEOUT_DONE)) break;
+            if (tcount > 0 && !tc::mbar_wait(drained, (tcount - 1) & 1, status, tc::TC_TIMEOUT_DONE, lim)) break;
             tc::tc_fence_after();
             for (int kk = 0; kk < nk; kk++, it++) {
                 const int s = it % STAGES;
-                if (!tc::mbar_wait(&full[s], (it / STAGES) & 1, status, tc::TC_TIMEOUT_FULL)) goto mma_done;
+                if (!tc::mbar_wait(&full[s], (it / STAGES) & 1, status, tc::TC_TIMEOUT_FULL, lim)) goto mma_done;
                 tc::tc_fence_after();
                 const uint32_t st = tc::smem_addr(smem + s * STAGE);
                 const uint32_t bh = st + AP * MT * A_TILE, bl = bh + B_TILE;
@@ -232,7 +235,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int quarter = warp & 3;
         uint32_t tcount = 0;
         for (int t = tile0; t < (MODE == 0 ? tile0 + 1 : ntiles); t += tstride, tcount++) {
-            bool ok = tc::mbar_wait(done, tcount & 1, status, tc::TC_TIMEOUT_DONE);
+            bool ok = tc::mbar_wait(done, tcount & 1, status, tc::TC_TIMEOUT_DONE, lim);
             tc::tc_fence_after();
             const int row = quarter * 32 + lane;
             if (MODE == 0) {
@@ -618,7 +621,14 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
     float *part = (float *)get_buf(ctx, BUF_TC_PART, sizeof(float) * size_t(nsplit) * Mrows * NP);
     double *C = (double *)get_buf(ctx, BUF_TC_C, sizeof(double) * size_t(n) * 2 * k);
     if (!part || !C) return HISQ_ERR_OOM;
+    // failure injection (tests): one call whose producers issue nothing and
+    // whose waits give up after a few thousand polls
+    const bool inject = ctx->inject_wait_timeout;
+    ctx->inject_wait_timeout = false;
+    const uint32_t lim = inject ? 4096u : tc::kSpinLimit;
     ExpandEpi none{};
+    none.spin_limit = lim;
+    none.no_loads = inject ? 1 : 0;
     const dim3 pgrid(nsplit, mgroups);
     auto project = [&](auto akc) -> hisq_status {
         constexpr int AKC = decltype(akc)::value;
@@ -642,7 +652,11 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
     HISQ_CUDA(cudaMemcpyAsync(Ch.data(), C, sizeof(double) * Ch.size(), cudaMemcpyDeviceToHost, ctx->stream));
     HISQ_CUDA(cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
-    if (hstatus != 0) return set_err(ctx, HISQ_ERR_TIMEOUT, "tensor-core projection: pipeline wait timed out (%d)", hstatus);
+    if (hstatus != 0)
+        return set_err(ctx, HISQ_ERR_TIMEOUT, "tensor-core projection: a pipeline wait ran out (code %d: %s)", hstatus,
+                       hstatus == tc::TC_TIMEOUT_FULL ? "operands never arrived"
+                                                      : (hstatus == tc::TC_TIMEOUT_EMPTY ? "stage never released"
+                                                                                          : "accumulator never ready"));
     const double shift = 4.0 * ctx->mass * ctx->mass;
     const int NE = 4 * k;                     // columns of the expansion
     const int NEP = ((NE + 15) / 16) * 16;
@@ -703,7 +717,7 @@ hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, 
         !make_tmap(&me[2], ddh, ldk, NEP, size_t(ldk) * 2, NT, bf) ||
         !make_tmap(&me[3], ddl, ldk, NEP, size_t(ldk) * 2, NT, bf))
         return set_err(ctx, HISQ_ERR_CUDA, "tensor map encoding failed");
-    ExpandEpi epi{(double2 *)X, update_r ? (double2 *)R : nullptr, fstride, desc, dfield, k, L};
+    ExpandEpi epi{lim, inject ? 1 : 0, (double2 *)X, update_r ? (double2 *)R : nullptr, fstride, desc, dfield, k, L};
     const int ntiles = (L + 127) / 128;
     const int grid = std::min(ntiles, ctx->num_sms);
     hisq_status st;

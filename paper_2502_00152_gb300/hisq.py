@@ -101,6 +101,9 @@ _PROTOS = [
     ("hisq_load_eigvecs", ctypes.c_int, [_CTX, ctypes.c_char_p]),
     ("hisq_set_profiling", ctypes.c_int, [_CTX, ctypes.c_int]),
     ("hisq_inject_alloc_failure", ctypes.c_int, [_CTX, ctypes.c_int]),
+    ("hisq_inject_wait_timeout", ctypes.c_int, [_CTX, ctypes.c_int]),
+    ("hisq_set_batched_kernel", ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("hisq_apply_dslash_batch", ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, ctypes.c_int, _DP, _DP]),
     ("hisq_bounds_violations", ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_int)]),
     ("hisq_device_bytes", ctypes.c_size_t, [_CTX]),
     ("hisq_kernel_launches", ctypes.c_ulonglong, [_CTX]),
@@ -341,6 +344,28 @@ def hisq_inject_alloc_failure(ctx: Context, after: int) -> None:
     """Host-side failure injection: device allocations fail after `after` more
     (after < 0 switches it off)."""
     _check(ctx.handle, load_library().hisq_inject_alloc_failure(ctx.handle, int(after)))
+
+
+def hisq_set_batched_kernel(ctx: Context, kind: int = 0, rhs_per_thread: int = 0, budget: int = 0) -> None:
+    """Launch shape of the batched operator: kind 0 autotuned; 1 register kernel
+    (budget 0/1/2 = 128/80/64 registers); 2 TMA-fed kernel (budget = blocks per SM)."""
+    _check(ctx.handle, load_library().hisq_set_batched_kernel(ctx.handle, kind, rhs_per_thread, budget))
+
+
+def hisq_apply_dslash_batch(ctx: Context, out_parity: int, precision: int, fields) -> np.ndarray:
+    """D on out_parity for host fields (nrhs, V, 3) through the batched operator."""
+    f = np.asarray(fields)
+    k = f.shape[0]
+    a = _field(f, ctx.V, k)
+    out = np.zeros((k, ctx.V, 3), dtype=np.complex128)
+    _check(ctx.handle, load_library().hisq_apply_dslash_batch(ctx.handle, out_parity, precision, k, _dp(a), _dp(out)))
+    return out
+
+
+def hisq_inject_wait_timeout(ctx: Context, on: bool = True) -> None:
+    """Failure injection: the next tensor-core deflation's GEMM issues no copy and
+    its bounded waits give up quickly (HISQ_ERR_TIMEOUT); one-shot."""
+    _check(ctx.handle, load_library().hisq_inject_wait_timeout(ctx.handle, 1 if on else 0))
 
 
 def hisq_set_profiling(ctx: Context, on: bool = True) -> None:

@@ -50,3 +50,28 @@ def test_batched_solve_uses_tc_deflation():
         assert H.hisq_kernel_launches(ctx) > launches0
     finally:
         ctx.close()
+
+
+def test_tc_wait_timeout_is_reported_and_recovered():
+    """The bounded waits of the tensor-core GEMM: with the producer told to issue
+    nothing and a short spin limit (host-set, one-shot), the MMA warp's wait for
+    its operands runs out with no copy and no MMA in flight; the call returns
+    HISQ_ERR_TIMEOUT with a message, and the same context then deflates
+    correctly."""
+    dims = (6, 6, 6, 8)
+    m = 0.01
+    ctx, o = make(dims, seed=21, eps=0.3, mass=m)
+    try:
+        lam, vecs = o.eig_dense(0.0, 40)
+        H.hisq_set_eigvecs(ctx, vecs, lam, 32)
+        bs = np.stack([project_parity(dims, I.gaussian_field(dims, 50 + j), 0) for j in range(5)])
+        H.hisq_inject_wait_timeout(ctx, True)
+        with pytest.raises(H.HisqError) as e:
+            H.hisq_deflate_batch(ctx, bs)
+        assert e.value.status == H.HISQ_ERR_TIMEOUT
+        assert "ran out" in str(e.value)
+        x, r = H.hisq_deflate_batch(ctx, bs)  # the injection was one-shot
+        for j in range(5):
+            assert rel(x[j], deflation_guess(vecs, lam + 4 * m * m, bs[j])) <= 1e-5
+    finally:
+        ctx.close()
