@@ -58,8 +58,11 @@ def parse():
     ap.add_argument("--n-ev", type=int, default=None)
     ap.add_argument("--n-kr", type=int, default=None)
     ap.add_argument("--cheby", type=int, default=60)
-    ap.add_argument("--amin", type=float, default=-2.0)
+    ap.add_argument("--amin", type=float, default=-2.0,
+                    help="Chebyshev window edge: > 0 given, -f: where about f n_ev eigenvalues lie below it")
     ap.add_argument("--eig-tol", type=float, default=1e-6)
+    ap.add_argument("--eig-cache", default=None, metavar="PATH",
+                    help="save the eigenpairs to PATH after the eigensolve, or reload them from it if it exists")
     ap.add_argument("--eig-block", type=int, default=64,
                     help="eigensolver block size (1: thick-restart Lanczos; b: block thick-restart Lanczos)")
     ap.add_argument("--eig-prec", type=int, default=None,
@@ -70,6 +73,9 @@ def parse():
     ap.add_argument("--plain-warmup", type=int, default=None,
                     help="warm-up steps of the plain-CG comparison (default: --warmup)")
     ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end host-API measurement")
+    ap.add_argument("--persistent", type=int, choices=[0, 1], default=0,
+                    help="batched solves: 1 = one cooperative launch per stretch of sloppy iterations, "
+                         "0 = three launches per iteration replayed as CUDA graphs")
     ap.add_argument("--source-pool-gb", type=float, default=30.0,
                     help="device memory for distinct source batches (cycled over the steps)")
     ap.add_argument("--cpu-iters", type=int, default=2, help="oracle CG iterations per CPU-baseline sample")
@@ -244,9 +250,20 @@ def run_ours(a):
     H.hisq_load_links(ctx, fat, lng, long_recon=a.recon, long_scale=I.C3_NAIK if a.recon != 18 else 1.0)
     H.hisq_set_mass(ctx, m)
 
-    # setup: eigensolve (excluded from the solve time, reported)
+    # setup: eigensolve (excluded from the solve time, reported), or the pairs
+    # of an earlier run reloaded from --eig-cache (eigenvalues recomputed as FP64
+    # Rayleigh quotients on load, as the paper recomputes them from stored vectors)
     eig = {}
-    if n_ev > 0:
+    cache_info = (a.eig_cache + ".json") if a.eig_cache else None
+    if n_ev > 0 and a.eig_cache and os.path.exists(a.eig_cache) and os.path.exists(cache_info):
+        torch.cuda.synchronize()
+        t0 = time.time()
+        H.hisq_load_eigvecs(ctx, a.eig_cache)
+        torch.cuda.synchronize()
+        with open(cache_info) as f:
+            eig = json.load(f)
+        eig["loaded_from_cache_seconds"] = round(time.time() - t0, 2)
+    elif n_ev > 0:
         ep = H.hisq_default_eig_params(n_ev=n_ev, n_kr=n_kr, tol=a.eig_tol, max_restarts=100, cheby_degree=a.cheby,
                                        a_min=a.amin, a_max=0.0, storage_precision=a.eig_prec, seed=1000 + rank,
                                        block_size=a.eig_block)
@@ -257,6 +274,10 @@ def run_ours(a):
         eig = dict(seconds=round(time.time() - t0, 2), n_ev=n_ev, n_kr=n_kr, block_size=a.eig_block,
                    converged=nconv, cheby_degree=a.cheby, eps_min=float(eps[0]), eps_max=float(eps[-1]),
                    storage=eig_name)
+        if a.eig_cache:
+            H.hisq_save_eigvecs(ctx, a.eig_cache)
+            with open(cache_info, "w") as f:
+                json.dump(eig, f)
 
     # sources: resident in HBM before the timed region (FP64 full-lattice fields)
     keep_links = (fat, lng) if (rank == 0 and world == 1 and not a.no_cpu_baseline) else (None, None)
@@ -284,7 +305,8 @@ def run_ours(a):
     rel_prec = a.reliable
     def params(deflate, rel):
         return H.hisq_default_solve_params(tol=tol, precision_sloppy=a.sloppy, link_precision_sloppy=a.links,
-                                           deflate=deflate, compute_full_residual=1, precision_reliable=rel)
+                                           deflate=deflate, compute_full_residual=1, precision_reliable=rel,
+                                           persistent=a.persistent)
     prm_defl = params(1 if n_ev > 0 else 0, rel_prec)
     prm_plain = params(0, rel_prec)
 
@@ -440,7 +462,10 @@ def run_ours(a):
             "sloppy_vectors": f"fp{a.sloppy}", "links": f"fp{a.links} recon {a.recon}",
             "l2": "inputs larger than L2 (links and eigenvectors are GBs)",
             "parallelism": f"replicas{world}",
-            "graphs": "on (CG iterations replayed as CUDA graphs on the library's stream)",
+            "graphs": ("off (persistent launch)" if a.persistent and kps > 1 else
+                       "on (CG iterations replayed as CUDA graphs on the library's stream)"),
+            "persistent": "on (one cooperative launch per stretch of sloppy iterations)" if a.persistent and kps > 1
+                          else "off",
             "sources": f"{nsrc} distinct batches resident in HBM, cycled over the steps",
         },
         "roofline": roof,
@@ -676,7 +701,7 @@ def run_learned(a):
     del fat, lng
     t0 = time.time()
     H.hisq_eigensolve(ctx, H.hisq_default_eig_params(n_ev=cfg["n_ev"], n_kr=int(1.5 * cfg["n_ev"]), tol=1e-6,
-                                                     max_restarts=100, cheby_degree=a.cheby, a_min=-2.0))
+                                                     max_restarts=100, cheby_degree=a.cheby, a_min=a.amin))
     t_eig = time.time() - t0
     prm = H.hisq_default_solve_params(deflate=1, batch=1, precision_sloppy=a.sloppy)
     par = torch.from_numpy((np.indices(dims[::-1]).sum(axis=0) & 1).reshape(-1)).cuda()

@@ -111,6 +111,16 @@ typedef struct {
                                 double-float links are built on first use and take
                                 as much device memory as the FP64 copy (2304 B per
                                 site); HISQ_ERR_OOM if they do not fit.  Default 64. */
+    int persistent;          /* batched solves (batch = 1, FP32 links with 18- or
+                                12-real long links): 1 runs the sloppy iterations
+                                between two host interventions (reliable updates,
+                                re-deflations, convergence) as one cooperative
+                                launch, all blocks resident, grid-wide phases
+                                separated by bounded barriers, stopping at the
+                                iteration in which a right-hand side reaches its
+                                next threshold; 0 (default) launches three kernels
+                                per iteration, replayed as CUDA graphs on a
+                                capturable stream.  Same arithmetic either way. */
 } hisq_solve_params;
 
 /* Per right-hand-side results of a solve. */
@@ -239,8 +249,10 @@ hisq_status hisq_solve_device(hisq_ctx *ctx, const double *eta_dev, double *psi_
  * Rayleigh-Ritz on the host, and final FP64 Rayleigh quotients with the FP64
  * operator (Section 3, eigenvalues recomputed from the eigenvectors).  eps_out
  * (nullable, n_ev doubles) receives the massless eigenvalues eps_i in ascending
- * order; *n_conv the number that met the tolerance.  The eigenvectors stay on
- * the device for deflation. */
+ * order; *n_conv the number that met the tolerance and whose FP64 residual
+ * |A v - eps v| / |v| is at most 1e-3 a_max (a pair that passes the filtered
+ * operator's test but not this one is spurious).  The eigenvectors stay on the
+ * device for deflation. */
 hisq_status hisq_eigensolve(hisq_ctx *ctx, const hisq_eig_params *params, int *n_conv,
                             double *eps_out);
 
@@ -319,12 +331,15 @@ hisq_status hisq_set_profiling(hisq_ctx *ctx, int on);
 hisq_status hisq_inject_alloc_failure(hisq_ctx *ctx, int after);
 
 /* Failure injection of a bounded device wait (tests of the timeout path; the
- * paper has no counterpart): with on != 0 the next tensor-core deflation
- * (hisq_deflate_batch, or the batched solve's) launches its GEMM with a producer
- * that issues no copy and with waits that give up after a few thousand polls,
- * so the MMA warp's wait for its operands runs out while no copy and no MMA is
- * in flight; the call returns HISQ_ERR_TIMEOUT with a message and the context
- * stays usable.  One-shot: the next call runs normally.  on = 0 cancels it. */
+ * paper has no counterpart): with on != 0 the next pipelined launch runs with
+ * a wait that cannot be met in time.  A tensor-core deflation
+ * (hisq_deflate_batch, or the batched solve's) launches its GEMM with a
+ * producer that issues no copy and with waits that give up after a few
+ * thousand polls, so the MMA warp's wait for its operands runs out while no
+ * copy and no MMA is in flight; a persistent batched CG launch runs its grid
+ * barriers with a zero time limit.  The call returns HISQ_ERR_TIMEOUT with a
+ * message and the context stays usable.  One-shot: the next call runs
+ * normally.  on = 0 cancels it. */
 hisq_status hisq_inject_wait_timeout(hisq_ctx *ctx, int on);
 
 /* Bounds checking (a stand-in for a memory checker): in a library built with

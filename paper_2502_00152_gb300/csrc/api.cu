@@ -162,6 +162,7 @@ void hisq_default_solve_params(hisq_solve_params *p)
     p->batch = 1;
     p->guess = 0;
     p->precision_reliable = 64;
+    p->persistent = 0;
 }
 
 void hisq_default_eig_params(hisq_eig_params *p)

@@ -26,12 +26,15 @@ hisq_status launch_defl_expand2(hisq_ctx *ctx, int n, int vprec, const void *V, 
 hisq_status tc_deflate_batch(hisq_ctx *ctx, int n, int k, double *R, double *X, const double *rnorm, const int *field,
                              bool update_r);
 
-// the tensor-core batched deflation applies to FP32- or BF16-stored
-// eigenvectors, up to 512 of them and 32 right-hand sides per call
+// the tensor-core batched deflation applies to FP32-, BF16- or FP16-stored
+// eigenvectors, up to 512 of them and 32 right-hand sides per call; with
+// 16-bit storage it also serves a single right-hand side (the GEMMs stream the
+// vectors near the HBM rate, and r is updated with the FP32 operator instead of
+// recomputing b - A x in FP64)
 static bool tc_eligible(const hisq_ctx *ctx, int n, int k)
 {
-    return (ctx->eig.prec == 32 || ctx->eig.prec == HISQ_PREC_BF16 || ctx->eig.prec == HISQ_PREC_HALF_EV) && n >= 1 &&
-           n <= 512 && k >= 2;
+    const bool prec_ok = ctx->eig.prec == 32 || ctx->eig.prec == HISQ_PREC_BF16 || ctx->eig.prec == HISQ_PREC_HALF_EV;
+    return prec_ok && n >= 1 && n <= 512 && (k >= 2 || (k == 1 && ctx->eig.prec != 32));
 }
 
 // r -= V c is the residual change of x += V Lambda^-1 c only while A v_i =
@@ -348,59 +351,111 @@ hisq_status solve_batched(hisq_ctx *ctx, const hisq_solve_params *P, const doubl
             }
         }
     };
+    // the persistent form of the iterations between host interventions
+    const bool persist = P->persistent && lprec == 32 && (prec == 16 || prec == 32) &&
+                         (ctx->long_recon == 12 || ctx->long_recon == 18);
+    std::vector<double> lo2(kMaxBatch, 0.0), hi2(kMaxBatch, 0.0), rrh(kMaxBatch, 0.0);
+    // one persistent launch up to the next iteration in which a right-hand side
+    // meets a condition the host acts on (the same conditions as below)
+    auto persistent_round = [&](std::vector<int> &upd) -> hisq_status {
+        long long mx = maxit - it;
+        for (int j : act) mx = std::min<long long>(mx, 1000 - (its[j] - last_upd[j]));
+        mx = std::max<long long>(1, std::min<long long>(mx, 1 << 30));
+        std::fill(lo2.begin(), lo2.end(), 0.0);
+        std::fill(hi2.begin(), hi2.end(), 0.0);
+        for (int j : act) {
+            const double lo = std::max(target[j], P->delta_rd * r_last[j]);
+            lo2[j] = lo * lo;
+            hi2[j] = 1e6 * r_last[j] * r_last[j];
+        }
+        int n = 0, itr[kMaxBatch] = {};
+        double ph[2] = {0, 0};
+        TRY(launch_bcg_persistent(ctx, prec, lprec, PP, TT, RS, XS, int(act.size()), int(mx), lo2.data(), hi2.data(),
+                                  &n, itr, prof ? ph : nullptr));
+        HISQ_CUDA(cudaMemcpyAsync(rrh.data(), ctx->bscal->rr, sizeof(double) * kMaxBatch, cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+        HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+        long long rhs_its = 0;
+        for (int j : act) {
+            its[j] += itr[j];
+            rhs_its += itr[j];
+        }
+        it += n;
+        if (prof && rhs_its > 0)
+            for (int j : act) { // launch time shared in proportion to each one's iterations
+                st[j].seconds_dslash_oe += ph[0] * itr[j] / double(rhs_its);
+                st[j].seconds_dslash_eo += ph[1] * itr[j] / double(rhs_its);
+                st[j].profiled_iterations += itr[j];
+            }
+        for (int j : act) {
+            const double rr = rrh[j];
+            if (!std::isfinite(rr)) return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite residual of right-hand side %d", j);
+            const double rn = std::sqrt(rr);
+            rn_seen[j] = rn;
+            if (rn < target[j] || rn < P->delta_rd * r_last[j] || rn > 1e3 * r_last[j] || its[j] - last_upd[j] >= 1000)
+                upd.push_back(j);
+        }
+        retired = it; // no per-launch events in this form
+        checked = it;
+        return HISQ_OK;
+    };
     while (!act.empty()) {
         const bool force = it >= maxit;
-        if (!force) {
-            const int ka = int(act.size());
-            const int slot = int(it & 3);
-            auto iteration = [&](bool cap) -> hisq_status {
-                if (prof) HISQ_CUDA(record_event(ctx, pe[slot][0], cap));
-                TRY(launch_mrhs_dslash_tt(ctx, prec, lprec, PP, TT, ka));
-                if (prof) HISQ_CUDA(record_event(ctx, pe[slot][1], cap));
-                TRY(launch_mrhs_dslash_update(ctx, prec, lprec, TT, PP, XS, RS, ka));
-                if (prof) HISQ_CUDA(record_event(ctx, pe[slot][2], cap));
-                TRY(launch_mrhs_p_update(ctx, prec, RS, PP, ka));
-                HISQ_CUDA(record_event(ctx, ev[slot & 1], cap));
-                return HISQ_OK;
-            };
-            // the first iteration of each active-set size runs directly (lazy
-            // kernel set-up happens outside capture), later ones replay a graph
-            if (ka != direct_ka) {
-                TRY(iteration(false));
-                direct_ka = ka;
-            } else {
-                TRY(graph_run(ctx, graphs, slot, ka, iteration));
-            }
-            act_at[it & 3] = act;
-            for (int j : act) its[j]++;
-            it++;
-        }
         std::vector<int> upd;
-        const long long jj = it - 2;
-        if (force) {
-            upd = act;
-        } else if (jj >= checked) {
-            HISQ_CUDA(cudaEventSynchronize(ev[jj & 1]));
-            if (*(volatile int *)ctx->wait_status_h != 0) {
-                const int code = *ctx->wait_status_h;
-                cudaStreamSynchronize(ctx->stream);
-                *ctx->wait_status_h = 0;
-                return set_err(ctx, HISQ_ERR_TIMEOUT, "batched operator: a pipeline wait ran out (code %d)", code);
-            }
-            retire(jj + 1);
-            for (int j : act_at[jj & 3]) {
-                const double rr = ctx->bmonitor_h[size_t(jj % ctx->bmonitor_len) * kMaxBatch + j];
-                if (!std::isfinite(rr)) {
-                    cudaStreamSynchronize(ctx->stream);
-                    return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite residual of right-hand side %d", j);
+        if (persist && !force) {
+            TRY(persistent_round(upd));
+        } else {
+            if (!force) {
+                const int ka = int(act.size());
+                const int slot = int(it & 3);
+                auto iteration = [&](bool cap) -> hisq_status {
+                    if (prof) HISQ_CUDA(record_event(ctx, pe[slot][0], cap));
+                    TRY(launch_mrhs_dslash_tt(ctx, prec, lprec, PP, TT, ka));
+                    if (prof) HISQ_CUDA(record_event(ctx, pe[slot][1], cap));
+                    TRY(launch_mrhs_dslash_update(ctx, prec, lprec, TT, PP, XS, RS, ka));
+                    if (prof) HISQ_CUDA(record_event(ctx, pe[slot][2], cap));
+                    TRY(launch_mrhs_p_update(ctx, prec, RS, PP, ka));
+                    HISQ_CUDA(record_event(ctx, ev[slot & 1], cap));
+                    return HISQ_OK;
+                };
+                // the first iteration of each active-set size runs directly (lazy
+                // kernel set-up happens outside capture), later ones replay a graph
+                if (ka != direct_ka) {
+                    TRY(iteration(false));
+                    direct_ka = ka;
+                } else {
+                    TRY(graph_run(ctx, graphs, slot, ka, iteration));
                 }
-                const double rn = std::sqrt(rr);
-                rn_seen[j] = rn;
-                if (rn < target[j] || rn < P->delta_rd * r_last[j] || rn > 1e3 * r_last[j] ||
-                    its[j] - last_upd[j] >= 1000)
-                    upd.push_back(j);
+                act_at[it & 3] = act;
+                for (int j : act) its[j]++;
+                it++;
             }
-            checked = jj + 1;
+            const long long jj = it - 2;
+            if (force) {
+                upd = act;
+            } else if (jj >= checked) {
+                HISQ_CUDA(cudaEventSynchronize(ev[jj & 1]));
+                if (*(volatile int *)ctx->wait_status_h != 0) {
+                    const int code = *ctx->wait_status_h;
+                    cudaStreamSynchronize(ctx->stream);
+                    *ctx->wait_status_h = 0;
+                    return set_err(ctx, HISQ_ERR_TIMEOUT, "batched operator: a pipeline wait ran out (code %d)", code);
+                }
+                retire(jj + 1);
+                for (int j : act_at[jj & 3]) {
+                    const double rr = ctx->bmonitor_h[size_t(jj % ctx->bmonitor_len) * kMaxBatch + j];
+                    if (!std::isfinite(rr)) {
+                        cudaStreamSynchronize(ctx->stream);
+                        return set_err(ctx, HISQ_ERR_NUMERICAL, "non-finite residual of right-hand side %d", j);
+                    }
+                    const double rn = std::sqrt(rr);
+                    rn_seen[j] = rn;
+                    if (rn < target[j] || rn < P->delta_rd * r_last[j] || rn > 1e3 * r_last[j] ||
+                        its[j] - last_upd[j] >= 1000)
+                        upd.push_back(j);
+                }
+                checked = jj + 1;
+            }
         }
         if (upd.empty()) continue;
         HISQ_CUDA(cudaStreamSynchronize(ctx->stream));

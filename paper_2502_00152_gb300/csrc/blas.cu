@@ -290,9 +290,9 @@ constexpr int kDeflSites = 4096;  // sites per block in the projection
 
 // partial[i][chunk] = sum over the chunk's sites of v_i^dag b
 // (16 vectors per block with unconditional loads was measured 1.8x slower:
-// at 128 registers it halves the resident blocks)
+// at 128 registers it halves the resident blocks; 8 vectors fit 80 registers)
 template <class SV, class SB>
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 3)
     k_defl_project(int Vh, int n, const char *__restrict__ V0, size_t vstride, SB b, double2 *part, int nchunks)
 {
     const int g0 = blockIdx.x * kDeflVG;
@@ -304,14 +304,18 @@ __global__ void __launch_bounds__(256, 4)
     for (int j = 0; j < kDeflVG; j++) ar[j] = ai[j] = 0.f;
     for (int cb = cb0 + threadIdx.x; cb < cb1; cb += blockDim.x) {
         CVec<float> bv = cvt<float>(b.load(cb));
+        // every vector's load is unconditional (a vector past n reads vector
+        // n - 1 and is not accumulated), so all of them are in flight at once
+        CVec<float> v[kDeflVG];
+#pragma unroll
+        for (int j = 0; j < kDeflVG; j++) v[j] = spinor_at<SV>(V0, vstride, min(g0 + j, n - 1), Vh).load(cb);
 #pragma unroll
         for (int j = 0; j < kDeflVG; j++) {
             if (g0 + j < n) {
-                CVec<float> v = spinor_at<SV>(V0, vstride, g0 + j, Vh).load(cb);
 #pragma unroll
                 for (int c = 0; c < 3; c++) {
-                    ar[j] = fmaf(v.re[c], bv.re[c], fmaf(v.im[c], bv.im[c], ar[j]));
-                    ai[j] = fmaf(v.re[c], bv.im[c], fmaf(-v.im[c], bv.re[c], ai[j]));
+                    ar[j] = fmaf(v[j].re[c], bv.re[c], fmaf(v[j].im[c], bv.im[c], ar[j]));
+                    ai[j] = fmaf(v[j].re[c], bv.im[c], fmaf(-v[j].im[c], bv.re[c], ai[j]));
                 }
             }
         }

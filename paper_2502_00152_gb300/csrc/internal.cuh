@@ -734,6 +734,7 @@ enum BufId : int {
     BUF_GUESS,         // even part of a caller's initial guess
     BUF_DF_X,          // double-float residual: x split into (hi, lo)
     BUF_DF_T,          // double-float residual: odd temporary D_oe x
+    BUF_PERSIST,       // persistent batched CG: per-block partials, thresholds
     BUF_COUNT
 };
 
@@ -1043,6 +1044,9 @@ hisq_status mrhs_set_identity(hisq_ctx *ctx, int k);
 hisq_status launch_mrhs_dslash_lin(hisq_ctx *ctx, int par, const void *in, void *out, double a, const void *x,
                                    double b, const void *y, double c, int k);
 hisq_status launch_mrhs_dslash_store(hisq_ctx *ctx, int par, int prec, const void *in, void *out, int k);
+hisq_status launch_bcg_persistent(hisq_ctx *ctx, int prec, int link_prec, void *p, void *tmp, void *r, void *x,
+                                  int kact, int max_iters, const double *lo2_h, const double *hi2_h, int *n_done,
+                                  int *its_rhs, double *phase_s);
 
 // double-float operator (df64.cu): fields of HISQ_PREC_DF64 storage
 hisq_status ensure_df_links(hisq_ctx *ctx);

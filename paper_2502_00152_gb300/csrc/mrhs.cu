@@ -143,12 +143,13 @@ template <class S, class SX>
 struct BEpiCG {
     BatchF<S> p, r;
     BatchF<SX> x;
-    const BatchScalars *scal;
+    const double *alpha; // alpha[j] by right-hand side (global or shared memory)
+    const double *m4;    // 4 m^2
     template <typename R>
     __device__ __forceinline__ void operator()(int cb, int j, const CVec<R> &acc, double &red) const
     {
-        const R alpha = R(scal->alpha[j]);
-        const R m4 = R(scal->m4);
+        const R alpha_j = R(alpha[j]);
+        const R m4v = R(*m4);
         const S pj = p.at(j), rj = r.at(j);
         const SX xj = x.at(j);
         CVec<R> pv = pj.load(cb);
@@ -157,12 +158,12 @@ struct BEpiCG {
         typedef typename SX::real XR;
 #pragma unroll
         for (int i = 0; i < 3; i++) {
-            R apr = fma(m4, pv.re[i], -acc.re[i]);
-            R api = fma(m4, pv.im[i], -acc.im[i]);
-            rv.re[i] = fma(-alpha, apr, rv.re[i]);
-            rv.im[i] = fma(-alpha, api, rv.im[i]);
-            xv.re[i] = fma(XR(alpha), XR(pv.re[i]), xv.re[i]);
-            xv.im[i] = fma(XR(alpha), XR(pv.im[i]), xv.im[i]);
+            R apr = fma(m4v, pv.re[i], -acc.re[i]);
+            R api = fma(m4v, pv.im[i], -acc.im[i]);
+            rv.re[i] = fma(-alpha_j, apr, rv.re[i]);
+            rv.im[i] = fma(-alpha_j, api, rv.im[i]);
+            xv.re[i] = fma(XR(alpha_j), XR(pv.re[i]), xv.re[i]);
+            xv.im[i] = fma(XR(alpha_j), XR(pv.im[i]), xv.im[i]);
         }
         xj.store(cb, xv);
         rj.store(cb, rv);
@@ -224,30 +225,45 @@ __device__ __forceinline__ void prefetch_long(const LinksF8 &L, int mu, int i)
     for (int k = 0; k < 4; k++) prefetch_l2(q + size_t(k) * L.Vh);
 }
 
-// PF: request the next direction's links into L2 while this one is computed
-// (15 prefetch instructions per thread and direction; the autotuner weighs them
-// against the latency they hide)
-template <int R, class S, class Lk, class L12T, bool R12, class Epi, bool PF = true>
-__global__ void __launch_bounds__(512, 1)
-    k_dslash_mrhs(Geom g, int par, Lk L, L12T L12, float c3, BatchF<S> in, const BatchScalars *scal, MrhsTile tl,
-                  Epi epi, BatchRed br)
+// gathered FP32 links of the batched kernels: fat (and, with 18-real long
+// links, long) rows per direction, read through the read-only path
+struct LinksFvB {
+    const float4 *base;
+    int Vh;
+    int nk;
+    typedef float real;
+    __device__ __forceinline__ void prefetch(int mu, int i) const
+    {
+        const float4 *q = base + size_t((mu * nk) * 9) * Vh + i;
+#pragma unroll
+        for (int k = 0; k < 9; k++) prefetch_l2(q + size_t(k) * Vh);
+    }
+    __device__ __forceinline__ void load(int mu, int kind, int i, CMat<float> &f, CMat<float> &b) const
+    {
+        const float4 *q = base + size_t((mu * nk + kind) * 9) * Vh + i;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            float4 a = __ldg(q + size_t(k) * Vh); // shared by the lanes of one site
+            f.re[k] = a.x;
+            f.im[k] = a.y;
+            b.re[k] = a.z;
+            b.im[k] = a.w;
+        }
+    }
+};
+
+// The sites of a batched operator launch: D on output parity `par` applied to
+// the R fields jj[] of `in` at this thread's sites (one site per lane, site
+// groups of 32 over the grid), each result handed to the epilogue with its
+// running reduction red[u].  Slots past kact (a partial last chunk) gather an
+// active field again and skip only the epilogue, so every gather is
+// unconditional and the compiler can issue them all ahead of the arithmetic.
+template <int R, class S, class Lk, class L12T, bool R12, class Epi, bool PF>
+__device__ __forceinline__ void mrhs_sites(const Geom &g, int par, const Lk &L, const L12T &L12, float c3,
+                                           const BatchF<S> &in, const int (&jj)[R], const bool (&on)[R],
+                                           const MrhsTile &tl, const Epi &epi, double (&red)[R])
 {
     typedef typename Lk::real Rl;
-    const int kact = scal->kact;
-    // slots past kact (a partial last chunk) gather an active field again and
-    // skip only the epilogue, so every gather is unconditional and the
-    // compiler can issue them all ahead of the arithmetic
-    int jj[R];
-    bool on[R];
-#pragma unroll
-    for (int u = 0; u < R; u++) {
-        const int q = tl.chunk() * R + u;
-        on[u] = q < kact; // uniform over the warp
-        jj[u] = scal->idx[on[u] ? q : kact - 1];
-    }
-    double red[R];
-#pragma unroll
-    for (int u = 0; u < R; u++) red[u] = 0;
     const int step = gridDim.x * tl.nsg * 32;
     for (int cb = (blockIdx.x * tl.nsg + tl.group()) * 32 + (threadIdx.x & 31); cb < g.Vh; cb += step) {
         int c[4];
@@ -303,7 +319,66 @@ __global__ void __launch_bounds__(512, 1)
         for (int u = 0; u < R; u++)
             if (on[u]) epi(cb, jj[u], acc[u], red[u]);
     }
+}
+
+// slots of this thread: chunk c holds slots c*R .. c*R+R-1
+template <int R>
+__device__ __forceinline__ void mrhs_slots(const BatchScalars *scal, const MrhsTile &tl, int kact, int (&jj)[R],
+                                           bool (&on)[R])
+{
+#pragma unroll
+    for (int u = 0; u < R; u++) {
+        const int q = tl.chunk() * R + u;
+        on[u] = q < kact; // uniform over the warp
+        jj[u] = scal->idx[on[u] ? q : kact - 1];
+    }
+}
+
+// PF: request the next direction's links into L2 while this one is computed
+// (15 prefetch instructions per thread and direction; the autotuner weighs them
+// against the latency they hide)
+template <int R, class S, class Lk, class L12T, bool R12, class Epi, bool PF = true>
+__global__ void __launch_bounds__(512, 1)
+    k_dslash_mrhs(Geom g, int par, Lk L, L12T L12, float c3, BatchF<S> in, const BatchScalars *scal, MrhsTile tl,
+                  Epi epi, BatchRed br)
+{
+    const int kact = scal->kact;
+    int jj[R];
+    bool on[R];
+    mrhs_slots<R>(scal, tl, kact, jj, on);
+    double red[R];
+#pragma unroll
+    for (int u = 0; u < R; u++) red[u] = 0;
+    mrhs_sites<R, S, Lk, L12T, R12, Epi, PF>(g, par, L, L12, c3, in, jj, on, tl, epi, red);
     batch_reduce<R>(red, tl, kact, br);
+}
+
+// p_j = r_j + beta_j p_j at this thread's sites for its R slots (jj[u] < 0:
+// inactive), |p_j|^2 into red[u]; beta by right-hand side (global or shared)
+template <int R, class S>
+__device__ __forceinline__ void pupd_sites(int Vh, const BatchF<S> &r, const BatchF<S> &p, const double *beta,
+                                           const int (&jj)[R], const MrhsTile &tl, double (&red)[R])
+{
+    typedef typename S::real Rl;
+    const int step = gridDim.x * tl.nsg * 32;
+    for (int cb = (blockIdx.x * tl.nsg + tl.group()) * 32 + (threadIdx.x & 31); cb < Vh; cb += step) {
+#pragma unroll
+        for (int u = 0; u < R; u++) {
+            if (jj[u] < 0) continue;
+            const int j = jj[u];
+            const Rl bj = Rl(beta[j]);
+            const S rj = r.at(j), pj = p.at(j);
+            auto rv = rj.load(cb);
+            auto pv = pj.load(cb);
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                pv.re[c] = fma(bj, pv.re[c], rv.re[c]);
+                pv.im[c] = fma(bj, pv.im[c], rv.im[c]);
+            }
+            pj.store(cb, pv);
+            red[u] += double(pv.norm2());
+        }
+    }
 }
 
 // p_j = r_j + beta_j p_j, |p_j|^2
@@ -311,7 +386,6 @@ template <int R, class S>
 __global__ void __launch_bounds__(512, 1)
     k_p_update_mrhs(int Vh, BatchF<S> r, BatchF<S> p, const BatchScalars *scal, MrhsTile tl, BatchRed br)
 {
-    typedef typename S::real Rl;
     const int kact = scal->kact;
     int jj[R];
 #pragma unroll
@@ -322,26 +396,231 @@ __global__ void __launch_bounds__(512, 1)
     double red[R];
 #pragma unroll
     for (int u = 0; u < R; u++) red[u] = 0;
-    const int step = gridDim.x * tl.nsg * 32;
-    for (int cb = (blockIdx.x * tl.nsg + tl.group()) * 32 + (threadIdx.x & 31); cb < Vh; cb += step) {
+    pupd_sites<R, S>(Vh, r, p, scal->beta, jj, tl, red);
+    batch_reduce<R>(red, tl, kact, br);
+}
+
+// ------------------------------------------------- persistent batched CG
+// The sloppy CG iterations of a batch between two host interventions (reliable
+// updates, re-deflations, convergence) in one cooperative launch, all blocks
+// resident.  Each iteration is three grid-wide phases as in the launch-per-phase
+// loop: tmp_j = D_oe p_j; the fused D_eo + update of x_j and r_j; p_j = r_j +
+// beta_j p_j.  Between phases a grid barrier (bounded: a wait that runs out
+// records its code in *status and every block leaves); after it every block
+// sums the per-block partials itself, in block order, so all blocks hold the
+// same alpha, beta and |p|^2 without another barrier.  The launch stops after
+// the iteration in which any right-hand side's |r|^2 leaves [lo2_j, hi2_j]
+// (the host's reliable-update, convergence and divergence thresholds) or is
+// not finite (the launch then ends two iterations later, see below), or after
+// max_iters iterations.
+struct PersistArgs {
+    double *part;              // [gridDim.x][3][kMaxBatch] per-block partial sums
+    unsigned *bar;             // grid barrier: [0] arrivals, [1] generation
+    int *status;               // bounded-wait status (0: fine)
+    const double *lo2, *hi2;   // thresholds by right-hand side
+    int max_iters;
+    double *monitor;           // host-mapped [monitor_len][kMaxBatch] |r|^2 history
+    int monitor_len;
+    unsigned long long *phase_ns; // [2]: time of the D_oe and D_eo phases (nullable)
+    int *iters_done;           // iterations of the launch
+    int *iters_rhs;            // iterations of each right-hand side (by id)
+    unsigned long long wait_ns; // a barrier wait longer than this gives up
+};
+
+constexpr int kGridWaitCode = 4;          // status code of a grid barrier that ran out
+constexpr unsigned long long kGridWaitNs = 4000000000ull; // 4 s
+
+// (A block that gives up still arrives at the barrier exactly once, so the
+// arrival counter returns to zero and the next launch starts clean.)
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded grid barrier: returns false when a wait ran out (here or elsewhere)
+__device__ __forceinline__ bool grid_sync(unsigned *bar, int *status, unsigned long long wait_ns)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned gen0 = *reinterpret_cast<volatile unsigned *>(&bar[1]);
+        __threadfence(); // this block's writes before the arrival
+        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicAdd(&bar[1], 1u);
+        } else {
+            const unsigned long long t0 = globaltimer_ns();
+            for (unsigned i = 0;; i++) {
+                if (*reinterpret_cast<volatile unsigned *>(&bar[1]) != gen0) break;
+                if ((i & 255) == 0) {
+                    if (*reinterpret_cast<volatile int *>(status) != 0 || globaltimer_ns() - t0 >= wait_ns) {
+                        atomicCAS(status, 0, kGridWaitCode);
+                        ok = 0;
+                        break;
+                    }
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence(); // the other blocks' writes after it (acquire)
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// per-slot sums of this block's R values per thread into out[slot]
+template <int R>
+__device__ __forceinline__ void block_partials(double (&v)[R], const MrhsTile &tl, int kact, double *out)
+{
+    __shared__ double sh[8][kMaxBatch];
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int u = 0; u < R; u++)
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) v[u] += __shfl_down_sync(0xffffffffu, v[u], o);
+    if (lane == 0) {
 #pragma unroll
         for (int u = 0; u < R; u++) {
-            if (jj[u] < 0) continue;
-            const int j = jj[u];
-            const Rl beta = Rl(scal->beta[j]);
-            const S rj = r.at(j), pj = p.at(j);
-            auto rv = rj.load(cb);
-            auto pv = pj.load(cb);
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                pv.re[c] = fma(beta, pv.re[c], rv.re[c]);
-                pv.im[c] = fma(beta, pv.im[c], rv.im[c]);
-            }
-            pj.store(cb, pv);
-            red[u] += double(pv.norm2());
+            const int q = tl.chunk() * R + u;
+            if (q < kMaxBatch) sh[tl.group()][q] = v[u];
         }
     }
-    batch_reduce<R>(red, tl, kact, br);
+    __syncthreads();
+    for (int q = threadIdx.x; q < kact; q += blockDim.x) {
+        double t = 0;
+        for (int w = 0; w < tl.nsg; w++) t += sh[w][q];
+        out[q] = t;
+    }
+    __syncthreads();
+}
+
+template <int R, class S, class SX, class L12T, bool R12>
+__global__ void __launch_bounds__(512, 1)
+    k_bcg_persistent(Geom g, LinksFvB Lo, LinksFvB Le, L12T L12o, L12T L12e, float c3, BatchF<S> p, BatchF<S> tmp,
+                     BatchF<S> r, BatchF<SX> x, BatchScalars *scal, MrhsTile tl, PersistArgs pa)
+{
+    __shared__ double alpha_s[kMaxBatch], beta_s[kMaxBatch], rr_s[kMaxBatch], rrn_s[kMaxBatch], pp_s[kMaxBatch];
+    __shared__ double m4_s;
+    __shared__ int idx_s[kMaxBatch], its_s[kMaxBatch], trig_s[kMaxBatch], ntrig_s;
+    const int kact = scal->kact;
+    for (int q = threadIdx.x; q < kact; q += blockDim.x) {
+        const int j = scal->idx[q];
+        idx_s[q] = j;
+        its_s[j] = trig_s[j] = 0;
+        rr_s[j] = scal->rr[j];
+        pp_s[j] = scal->pp[j];
+    }
+    if (threadIdx.x == 0) {
+        m4_s = scal->m4;
+        ntrig_s = 0;
+    }
+    __syncthreads();
+    int jj[R];
+    bool on[R];
+    mrhs_slots<R>(scal, tl, kact, jj, on);
+    const long long iter0 = scal->iter;
+    const bool timer = pa.phase_ns && blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long t_oe = 0, t_eo = 0;
+    double *part = pa.part + size_t(blockIdx.x) * 3 * kMaxBatch;
+    // sum of phase `ph`'s partials over the blocks, in block order (L2 reads)
+    auto grid_total = [&](int ph, int q) {
+        double t = 0;
+        for (int b = 0; b < int(gridDim.x); b++) t += __ldcg(pa.part + (size_t(b) * 3 + ph) * kMaxBatch + q);
+        return t;
+    };
+    // After the first iteration in which a right-hand side reaches its
+    // threshold, every right-hand side runs two more iterations (the host-driven
+    // loop notices a threshold two iterations late as well), so that the host
+    // takes the right-hand sides that reach theirs at about the same time at once.
+    int it = 0, first_trig = -1;
+    bool ok = true;
+    while (ok && it < pa.max_iters) {
+        unsigned long long ta = timer ? globaltimer_ns() : 0;
+        int jp[R]; // slots of the p update (-1: inactive)
+#pragma unroll
+        for (int u = 0; u < R; u++) jp[u] = on[u] ? jj[u] : -1;
+        double red[R];
+        // (1) tmp_j = D_oe p_j, |tmp_j|^2 -> alpha_j
+#pragma unroll
+        for (int u = 0; u < R; u++) red[u] = 0;
+        mrhs_sites<R, S, LinksFvB, L12T, R12, BEpiStore<S>, true>(g, 1, Lo, L12o, c3, p, jj, on, tl,
+                                                                  BEpiStore<S>{tmp}, red);
+        block_partials<R>(red, tl, kact, part);
+        if (!(ok = grid_sync(pa.bar, pa.status, pa.wait_ns))) break;
+        for (int q = threadIdx.x; q < kact; q += blockDim.x) {
+            const int j = idx_s[q];
+            alpha_s[j] = rr_s[j] / (m4_s * pp_s[j] + grid_total(0, q));
+        }
+        __syncthreads();
+        unsigned long long tb = timer ? globaltimer_ns() : 0;
+        // (2) Ap = 4m^2 p - D_eo tmp; x += alpha p; r -= alpha Ap; |r|^2 -> beta_j
+#pragma unroll
+        for (int u = 0; u < R; u++) red[u] = 0;
+        mrhs_sites<R, S, LinksFvB, L12T, R12, BEpiCG<S, SX>, true>(
+            g, 0, Le, L12e, c3, tmp, jj, on, tl, BEpiCG<S, SX>{p, r, x, alpha_s, &m4_s}, red);
+        block_partials<R>(red, tl, kact, part + kMaxBatch);
+        if (!(ok = grid_sync(pa.bar, pa.status, pa.wait_ns))) break;
+        for (int q = threadIdx.x; q < kact; q += blockDim.x) {
+            const int j = idx_s[q];
+            const double rn = grid_total(1, q);
+            rrn_s[j] = rn;
+            beta_s[j] = rn / rr_s[j];
+            trig_s[j] = !(rn >= pa.lo2[j] && rn <= pa.hi2[j]); // also NaN
+            if (blockIdx.x == 0 && pa.monitor)
+                pa.monitor[size_t((iter0 + it) % pa.monitor_len) * kMaxBatch + j] = rn;
+        }
+        __syncthreads();
+        if (timer) {
+            const unsigned long long tc = globaltimer_ns();
+            t_oe += tb - ta;
+            t_eo += tc - tb;
+        }
+        // (3) p_j = r_j + beta_j p_j, |p_j|^2
+#pragma unroll
+        for (int u = 0; u < R; u++) red[u] = 0;
+        pupd_sites<R, S>(g.Vh, r, p, beta_s, jp, tl, red);
+        block_partials<R>(red, tl, kact, part + 2 * kMaxBatch);
+        if (!(ok = grid_sync(pa.bar, pa.status, pa.wait_ns))) break;
+        for (int q = threadIdx.x; q < kact; q += blockDim.x) {
+            const int j = idx_s[q];
+            pp_s[j] = grid_total(2, q);
+            rr_s[j] = rrn_s[j];
+            its_s[j]++;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int q = 0; q < kact; q++)
+                if (trig_s[idx_s[q]]) ntrig_s++;
+        __syncthreads();
+        if (ntrig_s > 0 && first_trig < 0) first_trig = it;
+        it++;
+        if (first_trig >= 0 && it - first_trig > 2) break;
+    }
+    if (blockIdx.x == 0) {
+        for (int q = threadIdx.x; q < kact; q += blockDim.x) {
+            const int j = idx_s[q];
+            scal->rr[j] = rr_s[j];
+            scal->rr_new[j] = rr_s[j];
+            scal->pp[j] = pp_s[j];
+            scal->alpha[j] = alpha_s[j];
+            scal->beta[j] = beta_s[j];
+            pa.iters_rhs[j] = its_s[j];
+        }
+        if (threadIdx.x == 0) {
+            scal->iter = iter0 + it;
+            *pa.iters_done = it;
+            if (pa.phase_ns) {
+                pa.phase_ns[0] += t_oe;
+                pa.phase_ns[1] += t_eo;
+            }
+        }
+    }
 }
 
 // ------------------------------------------------- packed FP32 pairs
@@ -811,30 +1090,6 @@ static int mrhs_blocks_per_sm(K kern, int threads)
     return cache[slot];
 }
 
-struct LinksFvB {
-    const float4 *base;
-    int Vh;
-    int nk;
-    typedef float real;
-    __device__ __forceinline__ void prefetch(int mu, int i) const
-    {
-        const float4 *q = base + size_t((mu * nk) * 9) * Vh + i;
-#pragma unroll
-        for (int k = 0; k < 9; k++) prefetch_l2(q + size_t(k) * Vh);
-    }
-    __device__ __forceinline__ void load(int mu, int kind, int i, CMat<float> &f, CMat<float> &b) const
-    {
-        const float4 *q = base + size_t((mu * nk + kind) * 9) * Vh + i;
-#pragma unroll
-        for (int k = 0; k < 9; k++) {
-            float4 a = __ldg(q + size_t(k) * Vh); // shared by the lanes of one site
-            f.re[k] = a.x;
-            f.im[k] = a.y;
-            b.re[k] = a.z;
-            b.im[k] = a.w;
-        }
-    }
-};
 
 template <int P, class S, class Epi>
 static hisq_status run_mrhs_x2(hisq_ctx *ctx, int par, const BatchF<S> &in, const MrhsTile &tl, int pf, const Epi &epi,
@@ -1037,11 +1292,13 @@ hisq_status launch_mrhs_dslash_update(hisq_ctx *ctx, int prec, int link_prec, vo
     BatchRed br = batch_red(ctx, BFIN_BETA);
     switch (prec) {
     case 32: {
-        BEpiCG<SpinorF, SpinorF> epi{batchf<SpinorF>(p, Vh, 32), batchf<SpinorF>(r, Vh, 32), batchf<SpinorF>(x, Vh, 32), ctx->bscal};
+        BEpiCG<SpinorF, SpinorF> epi{batchf<SpinorF>(p, Vh, 32), batchf<SpinorF>(r, Vh, 32), batchf<SpinorF>(x, Vh, 32),
+                                     ctx->bscal->alpha, &ctx->bscal->m4};
         return run_mrhs(ctx, 0, link_prec, 32, batchf<SpinorF>(tmp, Vh, 32), kact, epi, br, false);
     }
     case 16: {
-        BEpiCG<SpinorH, SpinorF> epi{batchf<SpinorH>(p, Vh, 16), batchf<SpinorH>(r, Vh, 16), batchf<SpinorF>(x, Vh, 32), ctx->bscal};
+        BEpiCG<SpinorH, SpinorF> epi{batchf<SpinorH>(p, Vh, 16), batchf<SpinorH>(r, Vh, 16), batchf<SpinorF>(x, Vh, 32),
+                                     ctx->bscal->alpha, &ctx->bscal->m4};
         return run_mrhs(ctx, 0, link_prec, 16, batchf<SpinorH>(tmp, Vh, 16), kact, epi, br, false);
     }
     }
@@ -1088,6 +1345,114 @@ hisq_status launch_mrhs_dslash_lin(hisq_ctx *ctx, int par, const void *in, void 
                 y != nullptr};
     return run_mrhs(ctx, par, 32, 32, batchf<SpinorF>(const_cast<void *>(in), Vh, 32), k, epi,
                     batch_red(ctx, BFIN_STORE), false);
+}
+
+// The persistent batched CG (k_bcg_persistent) for the kact active slots: up
+// to max_iters iterations, stopping after the first iteration in which a
+// right-hand side's |r|^2 leaves [lo2_h[j], hi2_h[j]] (host arrays by RHS id)
+// and two more.
+// Synchronous: on return *n_done iterations have run, its_rhs[j] (host, by RHS
+// id) counts those of right-hand side j, and the batch scalars (rr, pp, alpha,
+// beta, iter) are those of each one's last iteration; phase_s (nullable)
+// accumulates the seconds of the D_oe and D_eo phases.  HISQ_ERR_TIMEOUT if a
+// grid barrier ran out.  The launch shape is the batch's tuned one.
+hisq_status launch_bcg_persistent(hisq_ctx *ctx, int prec, int link_prec, void *p, void *tmp, void *r, void *x,
+                                  int kact, int max_iters, const double *lo2_h, const double *hi2_h, int *n_done,
+                                  int *its_rhs, double *phase_s)
+{
+    const int Vh = ctx->g.Vh;
+    if (link_prec != 32 || (ctx->long_recon != 12 && ctx->long_recon != 18))
+        return set_err(ctx, HISQ_ERR_INVALID_ARG, "persistent batched CG: FP32 links with 18- or 12-real long links");
+    if (prec != 32 && prec != 16) return set_err(ctx, HISQ_ERR_INVALID_ARG, "persistent batched CG: sloppy 32 or 16");
+    if (kact < 1 || kact > kMaxBatch || max_iters < 1) return set_err(ctx, HISQ_ERR_INVALID_ARG, "persistent batched CG");
+    // the shape the autotuner picks for this batch (tuned on an ordinary D_oe
+    // launch the first time, which leaves nothing the persistent kernel reads)
+    if (!ctx->tuned.count(mrhs_key(ctx, kact, prec))) {
+        hisq_status st = launch_mrhs_dslash_tt(ctx, prec, link_prec, p, tmp, kact);
+        if (st != HISQ_OK) return st;
+    }
+    MrhsShape sh;
+    hisq_status st = mrhs_shape(ctx, kact, prec, &sh, false, nullptr);
+    if (st != HISQ_OK) return st;
+    if (sh.tma || sh.x2) return set_err(ctx, HISQ_ERR_INVALID_ARG, "persistent batched CG: register-kernel shapes only");
+    const MrhsTile tl = sh.tile;
+    const int threads = 32 * tl.nch * tl.nsg;
+    const bool r12 = ctx->long_recon == 12;
+    const LinksFvB Lo{ctx->links_f[1], Vh, r12 ? 1 : 2}, Le{ctx->links_f[0], Vh, r12 ? 1 : 2};
+    const LinksF12 L12o{r12 ? ctx->links_f12[1] : nullptr, Vh}, L12e{r12 ? ctx->links_f12[0] : nullptr, Vh};
+    const float c3 = float(ctx->long_scale);
+
+    auto go = [&](auto kern, auto tagS) -> hisq_status {
+        typedef decltype(tagS) S;
+        int bps = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, threads, 0) != cudaSuccess || bps < 1) {
+            cudaGetLastError();
+            return set_err(ctx, HISQ_ERR_CUDA, "persistent batched CG: occupancy query");
+        }
+        const int grid = grid_for(ctx, long(Vh), 32 * tl.nsg, bps); // every block resident
+        const size_t part_bytes = sizeof(double) * size_t(grid) * 3 * kMaxBatch;
+        char *buf = (char *)get_buf(ctx, BUF_PERSIST,
+                                    part_bytes + sizeof(double) * 2 * kMaxBatch + 64 + sizeof(int) * kMaxBatch);
+        if (!buf) return HISQ_ERR_OOM;
+        double *lo2 = (double *)(buf + part_bytes), *hi2 = lo2 + kMaxBatch;
+        unsigned long long *ns = (unsigned long long *)(hi2 + kMaxBatch);
+        int *done = (int *)(ns + 2);
+        int *its_d = done + 2;
+        HISQ_CUDA(cudaMemcpyAsync(lo2, lo2_h, sizeof(double) * kMaxBatch, cudaMemcpyHostToDevice, ctx->stream));
+        HISQ_CUDA(cudaMemcpyAsync(hi2, hi2_h, sizeof(double) * kMaxBatch, cudaMemcpyHostToDevice, ctx->stream));
+        HISQ_CUDA(cudaMemsetAsync(ns, 0, 2 * sizeof(unsigned long long), ctx->stream));
+        // failure injection (tests): a zero wait limit, so every block that waits
+        // at the first barrier gives up
+        const bool inject = ctx->inject_wait_timeout;
+        ctx->inject_wait_timeout = false;
+        PersistArgs pa{(double *)buf, ctx->ticket + 48, ctx->wait_status_d, lo2, hi2, max_iters, ctx->bmonitor_d,
+                       ctx->bmonitor_len, phase_s ? ns : nullptr, done, its_d, inject ? 0ull : kGridWaitNs};
+        BatchF<S> P = batchf<S>(p, Vh, prec), T = batchf<S>(tmp, Vh, prec), Rr = batchf<S>(r, Vh, prec);
+        BatchF<SpinorF> X = batchf<SpinorF>(x, Vh, 32);
+        Geom g = ctx->g;
+        float c3v = c3;
+        BatchScalars *scal = ctx->bscal;
+        MrhsTile tlv = tl;
+        LinksFvB lo = Lo, le = Le;
+        LinksF12 l12o = L12o, l12e = L12e;
+        void *args[] = {&g, &lo, &le, &l12o, &l12e, &c3v, &P, &T, &Rr, &X, &scal, &tlv, &pa};
+        cudaError_t e = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(kern), dim3(grid), dim3(threads),
+                                                    args, 0, ctx->stream);
+        if (e != cudaSuccess) return cuda_err(ctx, e, "persistent batched CG launch");
+        unsigned long long hns[2] = {0, 0};
+        int hdone = 0;
+        HISQ_CUDA(cudaMemcpyAsync(&hdone, done, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+        HISQ_CUDA(cudaMemcpyAsync(hns, ns, sizeof hns, cudaMemcpyDeviceToHost, ctx->stream));
+        HISQ_CUDA(cudaMemcpyAsync(its_rhs, its_d, sizeof(int) * kMaxBatch, cudaMemcpyDeviceToHost, ctx->stream));
+        HISQ_CUDA(cudaStreamSynchronize(ctx->stream));
+        if (*(volatile int *)ctx->wait_status_h != 0) {
+            const int code = *ctx->wait_status_h;
+            *ctx->wait_status_h = 0;
+            return set_err(ctx, HISQ_ERR_TIMEOUT, "persistent batched CG: a grid barrier ran out (code %d)", code);
+        }
+        *n_done = hdone;
+        if (phase_s) {
+            phase_s[0] += double(hns[0]) * 1e-9;
+            phase_s[1] += double(hns[1]) * 1e-9;
+        }
+        return HISQ_OK;
+    };
+    auto by_r = [&](auto tagS) -> hisq_status {
+        typedef decltype(tagS) S;
+        if (r12) {
+            switch (sh.R) {
+            case 2: return go(k_bcg_persistent<2, S, SpinorF, LinksF12, true>, S{});
+            case 3: return go(k_bcg_persistent<3, S, SpinorF, LinksF12, true>, S{});
+            default: return go(k_bcg_persistent<4, S, SpinorF, LinksF12, true>, S{});
+            }
+        }
+        switch (sh.R) {
+        case 2: return go(k_bcg_persistent<2, S, SpinorF, LinksF12, false>, S{});
+        case 3: return go(k_bcg_persistent<3, S, SpinorF, LinksF12, false>, S{});
+        default: return go(k_bcg_persistent<4, S, SpinorF, LinksF12, false>, S{});
+        }
+    };
+    return prec == 16 ? by_r(SpinorH{}) : by_r(SpinorF{});
 }
 
 // (3) p_j = r_j + beta_j p_j, pp_j (the shape of the batch's Dslash)

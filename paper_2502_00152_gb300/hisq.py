@@ -49,7 +49,8 @@ class hisq_solve_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision_sloppy", ctypes.c_int),
                 ("link_precision_sloppy", ctypes.c_int), ("delta_rd", ctypes.c_double), ("deflate", ctypes.c_int),
                 ("n_defl", ctypes.c_int), ("delta_tr", ctypes.c_double), ("compute_full_residual", ctypes.c_int),
-                ("batch", ctypes.c_int), ("guess", ctypes.c_int), ("precision_reliable", ctypes.c_int)]
+                ("batch", ctypes.c_int), ("guess", ctypes.c_int), ("precision_reliable", ctypes.c_int),
+                ("persistent", ctypes.c_int)]
 
 
 class hisq_solve_stats(ctypes.Structure):

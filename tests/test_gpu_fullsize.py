@@ -52,7 +52,7 @@ def test_deflation_many_chunks_matches_oracle(storage):
 # vectors and 24 right-hand sides; 200 FP16 vectors and 12 right-hand sides)
 # and the other template variants (FP32 high/low split; one A tile per CTA)
 @pytest.mark.parametrize("storage,n,k", [(H.HISQ_PREC_BF16, 512, 24), (H.HISQ_PREC_HALF_EV, 200, 12),
-                                         (H.HISQ_PREC_HALF_EV, 64, 24), (32, 130, 12)])
+                                         (H.HISQ_PREC_HALF_EV, 64, 24), (32, 130, 12), (H.HISQ_PREC_HALF_EV, 200, 1)])
 def test_tc_deflation_ring_and_tmem_reuse(storage, n, k):
     """12^3 x 16: L = 3 Vh = 41,472 rows.  The projection gives each of ~152
     CTAs >= 9 k-tiles of 64 (more than its 2 or 4 stages), the expansion 2-3
