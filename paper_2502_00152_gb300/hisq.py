@@ -255,15 +255,22 @@ def hisq_apply_normal_op(ctx: Context, precision: int, field, link_precision=Non
     return out
 
 
-def hisq_solve(ctx: Context, eta, params: Optional[hisq_solve_params] = None, guess=None):
+def hisq_solve(ctx: Context, eta, params: Optional[hisq_solve_params] = None, guess=None, out=None):
     """Solve M psi = eta for host field(s) eta ((V,3) or (nrhs,V,3)).  With
-    params.guess = 1, `guess` (same shape) is the initial guess.
+    params.guess = 1, `guess` (same shape) is the initial guess.  `out`
+    (optional, C-contiguous complex128 of eta's shape, e.g. a view of pinned
+    host memory) receives psi in place of a newly allocated array.
     Returns (psi, [stats dicts], status)."""
     eta = np.asarray(eta)
     single = eta.ndim == 2
     nrhs = 1 if single else eta.shape[0]
     e = _field(eta, ctx.V, nrhs)
-    psi = np.zeros((nrhs, ctx.V, 3), dtype=np.complex128)
+    if out is not None:
+        if out.dtype != np.complex128 or not out.flags.c_contiguous or out.size != nrhs * ctx.V * 3:
+            raise ValueError("out must be a C-contiguous complex128 array of eta's size")
+        psi = out.reshape(nrhs, ctx.V, 3)
+    else:
+        psi = np.zeros((nrhs, ctx.V, 3), dtype=np.complex128)
     if guess is not None:
         psi[:] = np.asarray(guess, dtype=np.complex128).reshape(psi.shape)
     p = params or hisq_default_solve_params()

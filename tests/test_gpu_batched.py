@@ -105,3 +105,25 @@ def test_batched_full_size_z2_walls():
             assert st[j]["iterations"] <= 0.9 * plain_it[j], (j, st[j]["iterations"], plain_it[j])
     finally:
         ctx.close()
+
+
+def test_host_solve_into_caller_buffer():
+    """hisq_solve writes into a caller-provided (e.g. pinned) output array: the
+    same solutions as with an array of its own."""
+    import torch
+
+    dims = (6, 6, 6, 8)
+    m = 0.01
+    ctx, o = make(dims, seed=21, eps=0.3, mass=m)
+    try:
+        etas = np.stack([I.gaussian_source(dims, 5, j) for j in range(3)])
+        prm = H.hisq_default_solve_params(batch=1, precision_sloppy=16)
+        psi, _, status = H.hisq_solve(ctx, etas, prm)
+        out = torch.full((3, I.volume(dims), 3), complex(np.nan, np.nan), dtype=torch.complex128).pin_memory()
+        psi2, _, status2 = H.hisq_solve(ctx, etas, prm, out=out.numpy())
+        assert status == status2 == H.HISQ_OK
+        assert np.array_equal(psi, out.numpy()) and np.shares_memory(psi2, out.numpy())
+        for j in range(3):
+            assert o.full_residual(m, out.numpy()[j], etas[j]) <= 1e-10
+    finally:
+        ctx.close()
