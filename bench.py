@@ -353,6 +353,7 @@ def run_ours(a):
 
     # headline: the deflated solve
     stats, elapsed_ms, value, launches, clk = timed(prm_defl, a.warmup, a.steps, profile=True, sample_clocks=True)
+    fp64_s, fp64_n = H.hisq_profiled_fp64(ctx)  # the FP64 Dslash launches of the timed steps
     if world > 1:
         torch.distributed.barrier()
     ms_per_step = elapsed_ms / a.steps  # one step = kps right-hand sides
@@ -423,7 +424,8 @@ def run_ours(a):
         tf = flops_site * Vh * rhs_launch / t_all / 1e12 if t_all > 0 else None
         roof = {
             "bound": "alu", "achieved": None if tf is None else round(tf, 2), "peak": round(peak32, 1),
-            "unit": "TFLOP/s", "frac": None if tf is None else round(tf / peak32, 4), "traffic": None,
+            "unit": "TFLOP/s", "frac": None if tf is None else round(tf / peak32, 4),
+            "traffic": ncu_traffic(f"mrhs{kps}_oe_s{a.sloppy}_r{a.recon}", Vh),
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (nominal clock)",
             "kernel": f"k_dslash_mrhs D_oe ({kps} RHS per launch)",
             "flops_per_rhs_site": flops_site,
@@ -437,6 +439,16 @@ def run_ours(a):
                                 if t_all_eo > 0 else None},
         }
 
+    # the FP64 Dslash (reliable-update residuals, source preparation, odd
+    # reconstruction, residual checks) is FP64-ALU bound: 1146 flop per output
+    # site against GB300's nominal 1.25 TFLOP/s FP64 rate
+    if fp64_n > 0 and fp64_s > 0:
+        tf64 = flops_site * Vh * fp64_n / fp64_s / 1e12
+        roof["fp64_dslash_kernel"] = {
+            "kernel": "k_dslash FP64 (reliable updates, source preparation, reconstruction, residual checks)",
+            "launches": fp64_n, "launch_us": round(fp64_s / fp64_n * 1e6, 2), "achieved_tflops": round(tf64, 3),
+            "peak": 1.25, "peak_source": "nominal GB300 dense FP64 rate", "frac": round(tf64 / 1.25, 4),
+            "share_of_timed": round(fp64_s * 1e3 / elapsed_ms, 4)}
     rel_name = "FP64 reliable updates" if rel_prec == 64 else "double-float reliable updates, final residual in FP64"
     out = {
         "metric": METRIC,
@@ -592,7 +604,7 @@ def run_capture(a):
 
     if a.traffic_from:
         out = os.path.join(ROOT, "profiles", "dslash_traffic.json")
-        write_traffic(a.traffic_from, a.config, a.traffic_key, out, a.traffic_command)
+        write_traffic(a.traffic_from, a.config, a.traffic_key, out, a.traffic_command, a.mrhs)
         return
     B.build()
     c = I.lattice_config(a.config)
@@ -633,11 +645,13 @@ def run_capture(a):
     ctx.close()
 
 
-def write_traffic(report: str, config: str, key: str, out: str, command: str) -> None:
-    """Per-output-site DRAM bytes of the D_oe (EpiXpay) and fused D_eo + update
-    (EpiCG) Dslash launches in an ncu report of this driver, written with the
-    hash of the Dslash sources they were taken on (the benchmark uses them only
-    while that hash matches)."""
+def write_traffic(report: str, config: str, key: str, out: str, command: str, mrhs: int = 0) -> None:
+    """Per-output-site DRAM bytes of the sloppy Dslash launches in an ncu report
+    of this driver: the single-RHS D_oe (EpiXpay) and fused D_eo + update (EpiCG)
+    kernels, or with mrhs = K the batched ones (BEpiStore, BEpiCG) for K
+    right-hand sides, keyed "mrhsK_...".  Entries are merged into `out` when it
+    was written on the same kernel sources (the hash of the Dslash sources is
+    stored with them; the benchmark uses them only while it matches)."""
     import csv
     import io
     import json
@@ -659,17 +673,34 @@ def write_traffic(report: str, config: str, key: str, out: str, command: str) ->
     per_site = {}
     for r in data:
         name = r[col["Kernel Name"]]
-        kind = "oe" if "EpiXpay" in name else ("eo" if "EpiCG" in name else None)
-        if kind is None:
+        if "k_dslash_mrhs" in name:
+            kind = "oe" if "BEpiStore" in name else ("eo" if "BEpiCG" in name else None)
+            prefix = f"mrhs{mrhs}_"
+        else:
+            kind = "oe" if "EpiXpay" in name else ("eo" if "EpiCG" in name else None)
+            prefix = ""
+        if kind is None or (prefix != "") != (mrhs > 1):
             continue
         b = sum(float(r[col[m]].replace(",", "")) * scale[units[col[m]]]
                 for m in ("dram__bytes_read.sum", "dram__bytes_write.sum"))
-        per_site.setdefault(f"{kind}_{key}", []).append(b / vh)
-    doc = {"what": f"DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per output site of the sloppy "
-                   f"Dslash kernels, from one ncu capture on the {dims_s} lattice (Vh = {vh}); traffic scales with "
-                   f"the number of output sites, so the benchmark multiplies by its own Vh",
-           "command": command, "kernel_source_hash": dslash_source_hash(),
-           "dram_bytes_per_output_site": {k: round(sum(v) / len(v), 1) for k, v in per_site.items()}}
+        per_site.setdefault(f"{prefix}{kind}_{key}", []).append(b / vh)
+    h = dslash_source_hash()
+    doc = {"what": "DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per output site of the sloppy Dslash "
+                   "kernels (keys mrhsK_...: the batched kernel for K right-hand sides), from ncu captures on the "
+                   f"{dims_s} lattice (Vh = {vh}); traffic scales with the number of output sites, so the benchmark "
+                   "multiplies by its own Vh",
+           "commands": [], "kernel_source_hash": h, "dram_bytes_per_output_site": {}}
+    try:
+        with open(out) as f:
+            old = json.load(f)
+        if old.get("kernel_source_hash") == h:
+            doc["commands"] = list(old.get("commands", []))
+            doc["dram_bytes_per_output_site"].update(old.get("dram_bytes_per_output_site", {}))
+    except (OSError, ValueError):
+        pass
+    if command and command not in doc["commands"]:
+        doc["commands"].append(command)
+    doc["dram_bytes_per_output_site"].update({k: round(sum(v) / len(v), 1) for k, v in per_site.items()})
     with open(out, "w") as f:
         json.dump(doc, f, indent=1)
     print(json.dumps(doc["dram_bytes_per_output_site"]))

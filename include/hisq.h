@@ -323,6 +323,12 @@ hisq_status hisq_load_eigvecs(hisq_ctx *ctx, const char *path);
  * every iteration; the sums are returned in hisq_solve_stats. */
 hisq_status hisq_set_profiling(hisq_ctx *ctx, int on);
 
+/* CUDA-event time (*seconds) and number (*launches) of the FP64 Dslash launches
+ * (reliable-update residuals, source preparation, odd reconstruction, residual
+ * checks) made while profiling was on, since it was last switched on.  Waits
+ * for the pending launches.  HISQ_ERR_INVALID_ARG for a null argument. */
+hisq_status hisq_profiled_fp64(hisq_ctx *ctx, double *seconds, unsigned long long *launches);
+
 /* Failure injection on the host (tests of the error paths; the paper has no
  * counterpart): after `after` further successful device allocations by this
  * context, every allocation fails as if the device were out of memory, so the

@@ -52,10 +52,11 @@ def _stamp(paths) -> str:
 
 
 def dslash_source_hash() -> str:
-    """Hash of the sources that determine the single-RHS Dslash kernels; a
-    stored ncu traffic figure is valid only for the hash it was taken on."""
+    """Hash of the sources that determine the single-RHS and batched Dslash
+    kernels; a stored ncu traffic figure is valid only for the hash it was
+    taken on."""
     h = hashlib.sha256()
-    for name in ("dslash.cu", "internal.cuh"):
+    for name in ("dslash.cu", "mrhs.cu", "internal.cuh"):
         with open(os.path.join(CSRC, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

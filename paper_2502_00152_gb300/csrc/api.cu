@@ -285,6 +285,11 @@ void hisq_destroy(hisq_ctx *ctx)
     cudaFree(ctx->bpartials);
     if (ctx->bmonitor_h) cudaFreeHost(ctx->bmonitor_h);
     if (ctx->wait_status_h) cudaFreeHost(ctx->wait_status_h);
+    for (auto &e : ctx->fp64_pending) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    for (cudaEvent_t e : ctx->fp64_pool) cudaEventDestroy(e);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
 }

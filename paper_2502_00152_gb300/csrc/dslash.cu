@@ -259,8 +259,61 @@ static hisq_status run_any(hisq_ctx *ctx, int par, int link_prec, const S &in, c
     return set_err(ctx, HISQ_ERR_INVALID_ARG, "FP32/FP16 links need FP32 or FP16 vectors");
 }
 
+void fp64_prof_drain(hisq_ctx *ctx, bool all, bool discard)
+{
+    size_t n = 0;
+    for (; n < ctx->fp64_pending.size(); n++) {
+        const auto &e = ctx->fp64_pending[n];
+        if (all || discard) {
+            cudaEventSynchronize(e.second);
+        } else if (cudaEventQuery(e.second) != cudaSuccess) {
+            cudaGetLastError(); // not ready yet: later pairs are not either
+            break;
+        }
+        float ms = 0;
+        if (!discard && cudaEventElapsedTime(&ms, e.first, e.second) == cudaSuccess) {
+            ctx->fp64_seconds += 1e-3 * ms;
+            ctx->fp64_launches++;
+        }
+        cudaGetLastError();
+        ctx->fp64_pool.push_back(e.first);
+        ctx->fp64_pool.push_back(e.second);
+    }
+    ctx->fp64_pending.erase(ctx->fp64_pending.begin(), ctx->fp64_pending.begin() + n);
+}
+
+static hisq_status dslash_xpay(hisq_ctx *ctx, int out_parity, int prec, int link_prec, const void *in, void *out,
+                               double a, const void *x, double b, const void *y, double c, int norm_slot);
+
+// With profiling on, an FP64 launch outside stream capture is bracketed by a
+// pair of events (from a pool); the pairs are summed once they have completed,
+// so the host never waits for a launch it has just issued.
 hisq_status launch_dslash(hisq_ctx *ctx, int out_parity, int prec, int link_prec, const void *in, void *out, double a,
                           const void *x, double b, const void *y, double c, int norm_slot)
+{
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (prec != 64 || !ctx->profile || cudaStreamIsCapturing(ctx->stream, &cap) != cudaSuccess ||
+        cap != cudaStreamCaptureStatusNone)
+        return dslash_xpay(ctx, out_parity, prec, link_prec, in, out, a, x, b, y, c, norm_slot);
+    cudaEvent_t e[2];
+    for (int i = 0; i < 2; i++) {
+        if (!ctx->fp64_pool.empty()) {
+            e[i] = ctx->fp64_pool.back();
+            ctx->fp64_pool.pop_back();
+        } else {
+            HISQ_CUDA(cudaEventCreate(&e[i]));
+        }
+    }
+    HISQ_CUDA(cudaEventRecord(e[0], ctx->stream));
+    const hisq_status st = dslash_xpay(ctx, out_parity, prec, link_prec, in, out, a, x, b, y, c, norm_slot);
+    HISQ_CUDA(cudaEventRecord(e[1], ctx->stream));
+    ctx->fp64_pending.emplace_back(e[0], e[1]);
+    fp64_prof_drain(ctx, ctx->fp64_pending.size() > 4096);
+    return st;
+}
+
+static hisq_status dslash_xpay(hisq_ctx *ctx, int out_parity, int prec, int link_prec, const void *in, void *out,
+                               double a, const void *x, double b, const void *y, double c, int norm_slot)
 {
     const int Vh = ctx->g.Vh;
     if (!ctx->links_loaded) return set_err(ctx, HISQ_ERR_STATE, "links not loaded");

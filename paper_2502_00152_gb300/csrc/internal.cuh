@@ -806,6 +806,13 @@ struct hisq_ctx {
     // a batched-operator launch shape chosen by the caller (0: autotuned)
     int mrhs_force_kind = 0, mrhs_force_R = 0, mrhs_force_budget = 0;
 
+    // profiling of the FP64 operator (hisq_set_profiling): event pairs around
+    // each FP64 Dslash launch, summed once their launches have completed
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> fp64_pending;
+    std::vector<cudaEvent_t> fp64_pool;
+    double fp64_seconds = 0;
+    unsigned long long fp64_launches = 0;
+
     // scratch buffers (grown on demand)
     void *bufs[hisq::BUF_COUNT] = {};
     size_t buf_cap[hisq::BUF_COUNT] = {};
@@ -1000,6 +1007,9 @@ hisq_status launch_convert(hisq_ctx *ctx, const void *in, int prec_in, void *out
 // FP16 sloppy links, built from the FP32 gathered links on first use (ingest.cu)
 hisq_status ensure_half_links(hisq_ctx *ctx);
 
+// FP64 operator timing: fold completed event pairs into the sums (all: wait
+// for every pending one); discard: drop them without summing
+void fp64_prof_drain(hisq_ctx *ctx, bool all, bool discard = false);
 hisq_status launch_dslash(hisq_ctx *ctx, int out_parity, int prec, int link_prec, const void *in,
                           void *out, double a, const void *x, double b, const void *y, double c,
                           int norm_slot);

@@ -565,7 +565,21 @@ hisq_status hisq_solve(hisq_ctx *ctx, const double *eta, double *psi, int nrhs, 
 hisq_status hisq_set_profiling(hisq_ctx *ctx, int on)
 {
     if (!ctx) return HISQ_ERR_INVALID_ARG;
+    if (on && !ctx->profile) { // the FP64 operator sums restart
+        fp64_prof_drain(ctx, true, true);
+        ctx->fp64_seconds = 0;
+        ctx->fp64_launches = 0;
+    }
     ctx->profile = on != 0;
+    return HISQ_OK;
+}
+
+hisq_status hisq_profiled_fp64(hisq_ctx *ctx, double *seconds, unsigned long long *launches)
+{
+    if (!ctx || !seconds || !launches) return HISQ_ERR_INVALID_ARG;
+    fp64_prof_drain(ctx, true);
+    *seconds = ctx->fp64_seconds;
+    *launches = ctx->fp64_launches;
     return HISQ_OK;
 }
 

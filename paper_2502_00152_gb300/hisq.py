@@ -101,6 +101,7 @@ _PROTOS = [
     ("hisq_save_eigvecs", ctypes.c_int, [_CTX, ctypes.c_char_p]),
     ("hisq_load_eigvecs", ctypes.c_int, [_CTX, ctypes.c_char_p]),
     ("hisq_set_profiling", ctypes.c_int, [_CTX, ctypes.c_int]),
+    ("hisq_profiled_fp64", ctypes.c_int, [_CTX, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_ulonglong)]),
     ("hisq_inject_alloc_failure", ctypes.c_int, [_CTX, ctypes.c_int]),
     ("hisq_inject_wait_timeout", ctypes.c_int, [_CTX, ctypes.c_int]),
     ("hisq_set_batched_kernel", ctypes.c_int, [_CTX, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -356,7 +357,9 @@ def hisq_inject_alloc_failure(ctx: Context, after: int) -> None:
 
 def hisq_set_batched_kernel(ctx: Context, kind: int = 0, rhs_per_thread: int = 0, budget: int = 0) -> None:
     """Launch shape of the batched operator: kind 0 autotuned; 1 register kernel
-    (budget 0/1/2 = 128/80/64 registers); 2 TMA-fed kernel (budget = blocks per SM)."""
+    with (budget 0) or without (1) the L2 prefetch of the next direction's links;
+    2 TMA-fed kernel (budget = blocks per SM, 2..4); 3 packed-pair kernel
+    (rhs_per_thread 2 or 4, budget as kind 1)."""
     _check(ctx.handle, load_library().hisq_set_batched_kernel(ctx.handle, kind, rhs_per_thread, budget))
 
 
@@ -382,6 +385,14 @@ def hisq_set_profiling(ctx: Context, on: bool = True) -> None:
 
 def hisq_device_bytes(ctx: Context) -> int:
     return int(load_library().hisq_device_bytes(ctx.handle))
+
+
+def hisq_profiled_fp64(ctx: Context):
+    """(seconds, launches) of the FP64 Dslash launches made while profiling was
+    on, CUDA-event timed."""
+    sec, n = ctypes.c_double(0), ctypes.c_ulonglong(0)
+    _check(ctx.handle, load_library().hisq_profiled_fp64(ctx.handle, ctypes.byref(sec), ctypes.byref(n)))
+    return sec.value, int(n.value)
 
 
 def hisq_kernel_launches(ctx: Context) -> int:

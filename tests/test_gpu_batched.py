@@ -127,3 +127,32 @@ def test_host_solve_into_caller_buffer():
             assert o.full_residual(m, out.numpy()[j], etas[j]) <= 1e-10
     finally:
         ctx.close()
+
+
+def test_fp64_operator_profiling():
+    """hisq_profiled_fp64 counts and times the FP64 Dslash launches made while
+    profiling is on: at least two per reliable update of every right-hand side
+    and one for each one's source preparation; switching profiling on again
+    restarts the sums, and nothing is counted while it is off."""
+    dims = (6, 6, 6, 8)
+    m = 0.01
+    ctx, o = make(dims, seed=21, eps=0.3, mass=m)
+    try:
+        etas = np.stack([I.gaussian_source(dims, 6, j) for j in range(3)])
+        prm = H.hisq_default_solve_params(batch=1, precision_sloppy=16)
+        H.hisq_set_profiling(ctx, True)
+        psi, st, status = H.hisq_solve(ctx, etas, prm)
+        H.hisq_set_profiling(ctx, False)
+        assert status == H.HISQ_OK
+        sec, n = H.hisq_profiled_fp64(ctx)
+        assert n >= 2 * sum(s["reliable_updates"] for s in st) + len(st), (n, st)
+        assert 0 < sec < sum(s["seconds_total"] for s in st) + 1.0
+        H.hisq_solve(ctx, etas, prm)  # profiling off: the sums stay
+        assert H.hisq_profiled_fp64(ctx) == (sec, n)
+        H.hisq_set_profiling(ctx, True)
+        assert H.hisq_profiled_fp64(ctx) == (0.0, 0)
+        H.hisq_set_profiling(ctx, False)
+        for j in range(3):
+            assert o.full_residual(m, psi[j], etas[j]) <= 1e-10
+    finally:
+        ctx.close()

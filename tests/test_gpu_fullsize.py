@@ -9,7 +9,10 @@ Small lattices leave some paths of the deflation and the eigensolver idle:
     expansion reuses its tensor-memory accumulator (the `drained` wait) only
     when a CTA gets two or more row tiles;
   * thick-restart Lanczos runs its stochastic window estimate, the Chebyshev
-    filter and the block-size reduction only at the benchmark's settings.
+    filter and the block-size reduction only at the benchmark's settings;
+  * the largest workload's lattice (64^3 x 96, Vh = 12,582,912) runs the
+    batched and FP64 operators with grids of many site groups per block, in
+    the benchmark's launch shape; they are compared over the whole lattice.
 Eq. 4 is a plain formula, so for these sizes the eigenvectors are host-QR
 orthonormal sets of seeded Gaussian even-site fields with chosen eigenvalues,
 for which the oracle's deflated guess is exact.  The eigensolver at 24^3 x 48 is
@@ -19,7 +22,7 @@ within the Kato-Temple bound."""
 import numpy as np
 import pytest
 
-from gpu_common import make, orthonormal_even_set, rel, stored_vectors
+from gpu_common import dslash_ref, make, orthonormal_even_set, rel, stored_vectors
 from oracle.oracle import deflation_guess, even_sites, project_parity, site_parity
 from paper_2502_00152_gb300 import hisq as H
 from paper_2502_00152_gb300 import inputs as I
@@ -136,5 +139,34 @@ def test_trlm_benchmark_settings_24c48():
         (e1, r1), (e2, r2) = runs
         bad = _kato_temple_ok(e1, r1, e2, r2)
         assert bad == [], bad[:5]
+    finally:
+        ctx.close()
+
+
+def test_operators_at_64c96():
+    """The largest workload's lattice (64^3 x 96, seed 4, eps 0.25, 12-real long
+    links): the batched operator on 12 Gaussian fields in the benchmark's launch
+    shape (3 right-hand sides per thread, next-direction link prefetch), with
+    FP16 and FP32 field storage, and the FP64 operator, on both output parities,
+    against the oracle's D over the whole lattice (fields 0, 7 and 11 of the
+    batch: first, middle and last chunk of right-hand sides)."""
+    c = I.lattice_config("c5")
+    dims = c["dims"]
+    ctx, o = make(dims, seed=c["seed"], eps=c["eps"], recon=12, mass=c["mass"])
+    try:
+        fields = np.stack([I.gaussian_field(dims, 500 + j) for j in range(12)])
+        for par in (1, 0):
+            refs = {j: dslash_ref(o, dims, fields[j], par) for j in (0, 7, 11)}
+            H.hisq_set_batched_kernel(ctx, 1, 3, 0)
+            try:
+                for prec, tol in ((16, 5e-3), (32, 1e-6)):
+                    out = H.hisq_apply_dslash_batch(ctx, par, prec, fields)
+                    for j, ref in refs.items():
+                        assert rel(out[j], ref) <= tol, (par, prec, j, rel(out[j], ref))
+                    del out
+            finally:
+                H.hisq_set_batched_kernel(ctx, 0)
+            x = H.hisq_apply_dslash(ctx, par, 64, fields[0])
+            assert rel(x, refs[0]) <= 1e-13, (par, rel(x, refs[0]))
     finally:
         ctx.close()
