@@ -143,30 +143,83 @@ def test_trlm_benchmark_settings_24c48():
         ctx.close()
 
 
-def test_operators_at_64c96():
-    """The largest workload's lattice (64^3 x 96, seed 4, eps 0.25, 12-real long
-    links): the batched operator on 12 Gaussian fields in the benchmark's launch
-    shape (3 right-hand sides per thread, next-direction link prefetch), with
-    FP16 and FP32 field storage, and the FP64 operator, on both output parities,
-    against the oracle's D over the whole lattice (fields 0, 7 and 11 of the
-    batch: first, middle and last chunk of right-hand sides)."""
+@pytest.fixture(scope="module")
+def lat64c96():
+    """The largest workload's lattice: 64^3 x 96, seed 4, eps 0.25, m = 0.0008,
+    12-real long links, on a context with a stream of its own (CUDA graphs on,
+    as in the benchmark)."""
     c = I.lattice_config("c5")
     dims = c["dims"]
     ctx, o = make(dims, seed=c["seed"], eps=c["eps"], recon=12, mass=c["mass"])
-    try:
-        fields = np.stack([I.gaussian_field(dims, 500 + j) for j in range(12)])
-        for par in (1, 0):
-            refs = {j: dslash_ref(o, dims, fields[j], par) for j in (0, 7, 11)}
-            H.hisq_set_batched_kernel(ctx, 1, 3, 0)
-            try:
-                for prec, tol in ((16, 5e-3), (32, 1e-6)):
-                    out = H.hisq_apply_dslash_batch(ctx, par, prec, fields)
-                    for j, ref in refs.items():
-                        assert rel(out[j], ref) <= tol, (par, prec, j, rel(out[j], ref))
-                    del out
-            finally:
-                H.hisq_set_batched_kernel(ctx, 0)
-            x = H.hisq_apply_dslash(ctx, par, 64, fields[0])
-            assert rel(x, refs[0]) <= 1e-13, (par, rel(x, refs[0]))
-    finally:
-        ctx.close()
+    yield ctx, o, dims, c["mass"]
+    ctx.close()
+
+
+def test_operators_at_64c96(lat64c96):
+    """The batched operator on 12 Gaussian fields in the benchmark's launch
+    shape (3 right-hand sides per thread, next-direction link prefetch), with
+    FP16 and FP32 field storage, and the FP64 operator, on both output
+    parities, against the oracle's D over the whole lattice (fields 0, 7 and 11
+    of the batch: first, middle and last chunk of right-hand sides)."""
+    ctx, o, dims, _ = lat64c96
+    fields = np.stack([I.gaussian_field(dims, 500 + j) for j in range(12)])
+    for par in (1, 0):
+        refs = {j: dslash_ref(o, dims, fields[j], par) for j in (0, 7, 11)}
+        H.hisq_set_batched_kernel(ctx, 1, 3, 0)
+        try:
+            for prec, tol in ((16, 5e-3), (32, 1e-6)):
+                out = H.hisq_apply_dslash_batch(ctx, par, prec, fields)
+                for j, ref in refs.items():
+                    assert rel(out[j], ref) <= tol, (par, prec, j, rel(out[j], ref))
+                del out
+        finally:
+            H.hisq_set_batched_kernel(ctx, 0)
+        x = H.hisq_apply_dslash(ctx, par, 64, fields[0])
+        assert rel(x, refs[0]) <= 1e-13, (par, rel(x, refs[0]))
+
+
+def _slab_vectors(dims, n, seed):
+    """n exactly orthonormal even-site fields: field i is a seeded Gaussian on
+    the even sites of timeslices 3i .. 3i+2 only, normalised, so the supports
+    are disjoint (no QR of a 38 M-row matrix needed)."""
+    X, Y, Z, T = dims
+    assert 3 * n <= T
+    slab = X * Y * Z
+    par = site_parity(dims)
+    vecs = np.zeros((n, int(np.prod(dims)), 3), dtype=np.complex128)
+    for i in range(n):
+        lo, hi = 3 * i * slab, (3 * i + 3) * slab
+        rng = np.random.default_rng(seed * 1000 + i)
+        w = rng.standard_normal((hi - lo, 3)) + 1j * rng.standard_normal((hi - lo, 3))
+        w[par[lo:hi] != 0] = 0
+        vecs[i, lo:hi] = w / np.linalg.norm(w)
+    return vecs
+
+
+def test_batched_deflated_solve_at_64c96(lat64c96):
+    """The benchmark's solve configuration on its lattice: 12 colour-diluted
+    Gaussian right-hand sides (4 sources x 3 colours) solved together with FP16
+    sloppy vectors, FP32 12-real links, FP64 reliable updates, re-deflation, CUDA
+    graphs and the autotuned batched operator, deflated with 32 stored vectors in
+    the FP16 v 2^e format (exactly orthonormal fields of disjoint support, with
+    Rayleigh quotients from the library), so the tensor-core projection and
+    expansion run at Vh = 12,582,912.  Every solution meets the 1e-10 true
+    residual under the oracle's operator."""
+    ctx, o, dims, m = lat64c96
+    vecs = _slab_vectors(dims, 32, seed=17)
+    H.hisq_set_eigvecs(ctx, vecs, None, H.HISQ_PREC_HALF_EV)
+    del vecs
+    etas = np.zeros((12, int(np.prod(dims)), 3), dtype=np.complex128)
+    for s in range(4):
+        src = I.gaussian_source(dims, 29, s)
+        for c in range(3):
+            etas[3 * s + c, :, c] = src[:, c]
+    del src
+    prm = H.hisq_default_solve_params(batch=1, deflate=1, precision_sloppy=16, compute_full_residual=1)
+    psi, st, status = H.hisq_solve(ctx, etas, prm)
+    assert status == H.HISQ_OK
+    for j in range(12):
+        assert st[j]["converged"] == 1 and st[j]["redeflations"] >= 1, (j, st[j])
+        res = o.full_residual(m, psi[j], etas[j])
+        assert res <= 1e-10, (j, res)
+        assert abs(st[j]["full_residual"] - res) <= 0.1 * res + 1e-15, (j, st[j]["full_residual"], res)

@@ -69,3 +69,30 @@ def test_persistent_barrier_timeout_is_reported_and_recovered():
             assert o.full_residual(m, psi[j], etas[j]) <= 1e-10
     finally:
         ctx.close()
+
+
+def test_persistent_full_size():
+    """32^3 x 64 (Vh = 1,048,576: every block of the cooperative grid walks many
+    site groups), the batched benchmark's lattice and mass, 12 Gaussian
+    right-hand sides with FP16 sloppy vectors, 12-real links and FP64 reliable
+    updates: every solution of the persistent form meets 1e-10 under the
+    oracle's operator, with iteration counts within a few of the
+    launch-per-phase form's."""
+    c = I.lattice_config("c2")
+    dims, m = c["dims"], c["mass"]
+    ctx, o = make(dims, seed=c["seed"], eps=c["eps"], recon=12, mass=m)
+    try:
+        etas = np.stack([I.gaussian_source(dims, 23, j) for j in range(12)])
+        runs = {}
+        for persistent in (0, 1):
+            prm = H.hisq_default_solve_params(batch=1, precision_sloppy=16, persistent=persistent)
+            psi, st, status = H.hisq_solve(ctx, etas, prm)
+            assert status == H.HISQ_OK
+            for j in range(12):
+                assert o.full_residual(m, psi[j], etas[j]) <= 1e-10, (persistent, j)
+            runs[persistent] = [s["iterations"] for s in st]
+        for j in range(12):
+            a, b = runs[0][j], runs[1][j]
+            assert abs(a - b) <= max(4, 0.02 * a), (j, a, b)
+    finally:
+        ctx.close()
