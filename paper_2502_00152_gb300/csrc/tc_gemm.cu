@@ -253,30 +253,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                 }
             } else {
+                // 32 accumulator columns (8 right-hand sides) at a time: the FP64
+                // x and r values of all 8 are loaded before the accumulator is
+                // read and before any store, so a thread has up to 16 loads in
+                // flight instead of one read-modify-write at a time
                 const int s = t * 128 + row;
-                for (int c0 = 0; c0 < N; c0 += 16) {
-                    float v[16];
-                    tc::tmem_ld16(taddr + (uint32_t(quarter * 32) << 16) + c0, v);
-                    if (ok && s < epi.rows) {
+                const bool live = ok && s < epi.rows;
+                const uint32_t tl = taddr + (uint32_t(quarter * 32) << 16);
+                for (int c0 = 0; c0 < N; c0 += 32) {
+                    double2 xv[8], rv[8];
+                    double2 *xp[8], *rp[8];
 #pragma unroll
-                        for (int i = 0; i < 16; i += 4) {
-                            const int j = (c0 + i) >> 2;
-                            if (j < epi.k) {
-                                const float *sc = epi.scale + 4 * j;
-                                const size_t f = size_t(epi.field[j]);
-                                double2 *xp = epi.x + epi.fstride * f + s;
-                                double2 xv = *xp;
-                                xv.x += double(v[i + 0]) * sc[0];
-                                xv.y += double(v[i + 1]) * sc[1];
-                                *xp = xv;
-                                if (epi.r) {
-                                    double2 *rp = epi.r + epi.fstride * f + s;
-                                    double2 rv = *rp;
-                                    rv.x -= double(v[i + 2]) * sc[2];
-                                    rv.y -= double(v[i + 3]) * sc[3];
-                                    *rp = rv;
-                                }
+                    for (int q = 0; q < 8; q++) {
+                        const int j = (c0 >> 2) + q; // columns 4j .. 4j+3 belong to right-hand side j
+                        xp[q] = nullptr;
+                        rp[q] = nullptr;
+                        if (live && j < epi.k) {
+                            const size_t f = size_t(epi.field[j]);
+                            xp[q] = epi.x + epi.fstride * f + s;
+                            xv[q] = *xp[q];
+                            if (epi.r) {
+                                rp[q] = epi.r + epi.fstride * f + s;
+                                rv[q] = *rp[q];
                             }
+                        }
+                    }
+                    float v0[16], v1[16];
+                    tc::tmem_ld16(tl + c0, v0); // warp-wide: c0 and N are uniform
+                    if (c0 + 16 < N) {
+                        tc::tmem_ld16(tl + c0 + 16, v1);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; i++) v1[i] = 0.f;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        if (!xp[q]) continue;
+                        const float *sc = epi.scale + 4 * ((c0 >> 2) + q);
+                        const float *v = q < 4 ? v0 + 4 * q : v1 + 4 * (q - 4);
+                        xv[q].x += double(v[0]) * sc[0];
+                        xv[q].y += double(v[1]) * sc[1];
+                        *xp[q] = xv[q];
+                        if (rp[q]) {
+                            rv[q].x -= double(v[2]) * sc[2];
+                            rv[q].y -= double(v[3]) * sc[3];
+                            *rp[q] = rv[q];
                         }
                     }
                 }
