@@ -10,7 +10,7 @@ sides (colour-vector fields) in, three guesses out.
 
 The guess enters the solve through hisq_solve_params.guess: CG starts from it
 (its residual deflated when deflation is on) and still runs to the same FP64
-true residual, so the plain solve remains both the fallback and the judge.
+true residual, so the plain solve remains both the fallback and the arbiter.
 """
 from __future__ import annotations
 
