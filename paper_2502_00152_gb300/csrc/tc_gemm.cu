@@ -120,18 +120,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     constexpr int B_TILE = N * TC_ROWB;
     constexpr int AP = AK == AK_F16_SPLIT ? 2 : 1;        // A parts: hi (+ lo for split FP32)
     constexpr int STAGE = AP * MT * A_TILE + 2 * B_TILE;  // B: hi + lo
-    constexpr int NCOLS = (MT * N <= 32) ? 32 : (MT * N <= 64) ? 64 : (MT * N <= 128) ? 128 : (MT * N <= 256) ? 256 : 512;
+    // the expansion walks several row tiles per CTA: two accumulators, so that the
+    // MMAs of tile t+1 run while the epilogue drains tile t
+    constexpr int NBUF = MODE == 1 ? 2 : 1;
+    constexpr int BUFC = MT * N; // TMEM columns of one accumulator
+    constexpr int NCOLS = (NBUF * BUFC <= 32) ? 32 : (NBUF * BUFC <= 64) ? 64 : (NBUF * BUFC <= 128) ? 128
+                        : (NBUF * BUFC <= 256) ? 256 : 512;
     constexpr uint32_t IDESC = AK == AK_BF16 ? tc::idesc_bf16_f32(128, N) : tc::idesc_f16_f32(128, N);
     static_assert(N % 16 == 0 && N >= 16 && N <= 256, "N");
-    static_assert(MT * N <= 512, "TMEM columns");
+    static_assert(NBUF * BUFC <= 512, "TMEM columns");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE);
     uint64_t *empty = full + STAGES;
-    uint64_t *done = empty + STAGES;     // MMAs of a tile finished
-    uint64_t *drained = done + 1;        // epilogue has read the accumulator
-    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(drained + 1);
+    uint64_t *done = empty + STAGES;     // [NBUF] MMAs of a tile finished
+    uint64_t *drained = done + NBUF;     // [NBUF] epilogue has read the accumulator
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(drained + NBUF);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -139,8 +144,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
-        tc::mbar_init(done, 1);
-        tc::mbar_init(drained, 128);
+        for (int b = 0; b < NBUF; b++) {
+            tc::mbar_init(&done[b], 1);
+            tc::mbar_init(&drained[b], 128);
+        }
         tc::fence_mbar_init();
     }
     if (warp == 1) tc::tmem_alloc(tmem_holder, NCOLS);
@@ -201,7 +208,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---------------- MMA issuer
         uint32_t it = 0, tcount = 0;
         for (int t = tile0; t < (MODE == 0 ? tile0 + 1 : ntiles); t += tstride, tcount++) {
-            if (tcount > 0 && !tc::mbar_wait(drained, (tcount - 1) & 1, status, tc::TC_TIMEOUT_DONE, lim)) break;
+            // accumulator b is used for the (use)-th time: the epilogue must have
+            // drained its previous use
+            const uint32_t b = tcount % NBUF, use = tcount / NBUF;
+            if (use > 0 && !tc::mbar_wait(&drained[b], (use - 1) & 1, status, tc::TC_TIMEOUT_DONE, lim)) break;
             tc::tc_fence_after();
             for (int kk = 0; kk < nk; kk++, it++) {
                 const int s = it % STAGES;
@@ -215,7 +225,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int q = 0; q < TC_BK / 16; q++) {
                         const uint32_t off = q * 32; // 16 16-bit values along K inside the swizzle atom
-                        const uint32_t d = taddr + mt * N;
+                        const uint32_t d = taddr + b * BUFC + mt * N;
                         const uint32_t acc0 = (kk > 0 || q > 0) ? 1u : 0u;
                         tc::mma_f16(d, tc::smem_desc_sw128(ah + off), tc::smem_desc_sw128(bh + off), IDESC, acc0);
                         tc::mma_f16(d, tc::smem_desc_sw128(ah + off), tc::smem_desc_sw128(bl + off), IDESC, 1u);
@@ -225,7 +235,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc::mma_commit(&empty[s]);
             }
-            tc::mma_commit(done);
+            tc::mma_commit(&done[b]);
         }
     mma_done:;
     }
@@ -235,8 +245,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int quarter = warp & 3;
         uint32_t tcount = 0;
         for (int t = tile0; t < (MODE == 0 ? tile0 + 1 : ntiles); t += tstride, tcount++) {
-            bool ok = tc::mbar_wait(done, tcount & 1, status, tc::TC_TIMEOUT_DONE, lim);
+            const uint32_t b = tcount % NBUF, use = tcount / NBUF;
+            bool ok = tc::mbar_wait(&done[b], use & 1, status, tc::TC_TIMEOUT_DONE, lim);
             tc::tc_fence_after();
+            const uint32_t tbuf = taddr + b * BUFC;
             const int row = quarter * 32 + lane;
             if (MODE == 0) {
                 for (int mt = 0; mt < MT; mt++) {
@@ -244,7 +256,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
                     for (int c0 = 0; c0 < N; c0 += 16) {
                         float v[16];
-                        tc::tmem_ld16(taddr + (uint32_t(quarter * 32) << 16) + mt * N + c0, v);
+                        tc::tmem_ld16(tbuf + (uint32_t(quarter * 32) << 16) + mt * N + c0, v);
                         if (ok && nk > 0 && m < Mrows) {
                             float *dst = part + (size_t(blockIdx.x) * Mrows + m) * N + c0;
 #pragma unroll
@@ -259,7 +271,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 // flight instead of one read-modify-write at a time
                 const int s = t * 128 + row;
                 const bool live = ok && s < epi.rows;
-                const uint32_t tl = taddr + (uint32_t(quarter * 32) << 16);
+                const uint32_t tl = tbuf + (uint32_t(quarter * 32) << 16);
                 for (int c0 = 0; c0 < N; c0 += 32) {
                     double2 xv[8], rv[8];
                     double2 *xp[8], *rp[8];
@@ -303,7 +315,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             }
             tc::tc_fence_before();
-            tc::mbar_arrive(drained);
+            tc::mbar_arrive(&drained[b]);
         }
     }
     __syncthreads();
