@@ -116,9 +116,11 @@ typedef struct {
                                 between two host interventions (reliable updates,
                                 re-deflations, convergence) as one cooperative
                                 launch, all blocks resident, grid-wide phases
-                                separated by bounded barriers, stopping at the
-                                iteration in which a right-hand side reaches its
-                                next threshold; 0 (default) launches three kernels
+                                separated by bounded barriers, handing the batch
+                                back two iterations after the first right-hand
+                                side reaches its next threshold (the launch-per-
+                                iteration loop also sees each residual two
+                                iterations late); 0 (default) launches three kernels
                                 per iteration, replayed as CUDA graphs on a
                                 capturable stream.  Same arithmetic either way. */
 } hisq_solve_params;
@@ -135,7 +137,9 @@ typedef struct {
     double seconds_total;    /* prep + deflation + CG + reconstruction             */
     double seconds_deflate;  /* initial deflation and re-deflations                */
     /* filled only with profiling on (hisq_set_profiling): CUDA-event time of the
-       two Dslash kernels of each sloppy CG iteration, summed over iterations    */
+       two Dslash kernels of each sloppy CG iteration, summed over iterations; in
+       a batched solve each launch's time is shared equally among the right-hand
+       sides it served                                                           */
     double seconds_dslash_oe; /* tmp = D_oe p, |tmp|^2                          */
     double seconds_dslash_eo; /* 4m^2 p - D_eo tmp fused with the x, r update    */
     int profiled_iterations;
@@ -153,7 +157,8 @@ typedef struct {
                                 a_min > 0: given; a_min = -f < 0: placed where an
                                 estimated f * n_ev eigenvalues lie below it (0: f = 2) */
     double a_max;            /* > 0: given; <= 0: 1.1 x a power-iteration estimate  */
-    int storage_precision;   /* eigenvector storage: 32, 16 or HISQ_PREC_BF16 (15)    */
+    int storage_precision;   /* eigenvector storage: 32, 16, HISQ_PREC_BF16 (15) or
+                                HISQ_PREC_HALF_EV (14)                              */
     uint64_t seed;           /* start vector                                        */
     int block_size;          /* 1: thick-restart Lanczos; b = 2..64: block thick-restart
                                 Lanczos with b vectors per step, the operator applied to
@@ -246,7 +251,9 @@ hisq_status hisq_solve_device(hisq_ctx *ctx, const double *eta_dev, double *psi_
 
 /* Thick-restart Lanczos for the lowest n_ev eigenpairs of the massless even-site
  * operator -D_eo D_oe (Section 2), with FP32 operator and basis, FP64
- * Rayleigh-Ritz on the host, and final FP64 Rayleigh quotients with the FP64
+ * Rayleigh-Ritz (tridiagonal QL on the host for block_size 1, a dense FP64
+ * Hermitian eigensolver on the device for the block variant), and final FP64
+ * Rayleigh quotients with the FP64
  * operator (Section 3, eigenvalues recomputed from the eigenvectors).  eps_out
  * (nullable, n_ev doubles) receives the massless eigenvalues eps_i in ascending
  * order; *n_conv the number that met the tolerance and whose FP64 residual
@@ -264,7 +271,8 @@ hisq_status hisq_get_eigvec(hisq_ctx *ctx, int i, double *out);
 
 /* Replace the stored eigenpairs by n host fields (even sites used; orthonormal)
  * with massless eigenvalues eps (nullable: recomputed as FP64 Rayleigh
- * quotients), stored at storage_precision 32, 16 or 15 (BF16). */
+ * quotients), stored at storage_precision 32, 16, 15 (BF16) or 14
+ * (HISQ_PREC_HALF_EV). */
 hisq_status hisq_set_eigvecs(hisq_ctx *ctx, int n, const double *vecs, const double *eps,
                              int storage_precision);
 
@@ -320,7 +328,9 @@ hisq_status hisq_load_eigvecs(hisq_ctx *ctx, const char *path);
 
 /* Turn per-kernel CUDA-event timing of the CG iterations on (1) or off (0).
  * Events are recorded on the context's stream around the two Dslash kernels of
- * every iteration; the sums are returned in hisq_solve_stats. */
+ * every iteration (sums returned in hisq_solve_stats) and around every FP64
+ * Dslash launch (sums returned by hisq_profiled_fp64, restarted each time
+ * profiling is switched on).  Launches inside a stream capture are not timed. */
 hisq_status hisq_set_profiling(hisq_ctx *ctx, int on);
 
 /* CUDA-event time (*seconds) and number (*launches) of the FP64 Dslash launches
