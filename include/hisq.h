@@ -330,7 +330,8 @@ hisq_status hisq_load_eigvecs(hisq_ctx *ctx, const char *path);
  * Events are recorded on the context's stream around the two Dslash kernels of
  * every iteration (sums returned in hisq_solve_stats) and around every FP64
  * Dslash launch (sums returned by hisq_profiled_fp64, restarted each time
- * profiling is switched on).  Launches inside a stream capture are not timed. */
+ * profiling is switched on; an FP64 launch made during a stream capture is not
+ * timed). */
 hisq_status hisq_set_profiling(hisq_ctx *ctx, int on);
 
 /* CUDA-event time (*seconds) and number (*launches) of the FP64 Dslash launches
